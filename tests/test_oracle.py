@@ -1,0 +1,374 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+None of these checks re-types the oracle's own formulas: each compares the oracle
+with an independent route (direct lattice sums, a closed-form convolution, a
+library SVD/solve, brute force on tiny grids, exact algebraic identities).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import spm_inputs as si
+from oracle import radial
+
+pytestmark = pytest.mark.filterwarnings("ignore::RuntimeWarning")
+
+
+# --------------------------------------------------------------- lattice sum
+
+@pytest.mark.parametrize("s", [2.0, 3.0])
+def test_lattice_zeta_matches_direct_sum(s):
+    """Mellin/Poisson continuation equals the convergent direct sum where one exists."""
+    R = 48
+    r = np.arange(-R, R + 1)
+    X, Y, Z = np.meshgrid(r, r, r, indexing="ij")
+    rr = np.sqrt(X * X + Y * Y + Z * Z)
+    rr = rr[(rr > 0) & (rr <= R)]
+    direct = np.sum(rr ** (-2 * s)) + 4 * np.pi * R ** (3 - 2 * s) / (2 * s - 3)
+    assert abs(oracle.lattice_zeta(s) - direct) < 2e-5 * direct
+
+
+def test_punctured_trapezoid_h2_coefficient_is_lattice_constant():
+    """The punctured trapezoidal rule for int f/r has error h^2 Z f(0) + O(h^4).
+
+    This is the expansion the order-4 correction G_0 = h^2 (ikh - Z)/(4 pi) removes;
+    the Gaussian integral int e^{-r^2/s^2}/r = 2 pi s^2 is exact.
+    """
+    Zc = oracle.lattice_zeta(0.5)
+    s = 0.3
+    coef = []
+    for h in (0.05, 0.025):
+        R = int(8 * s / h) + 1
+        r = np.arange(-R, R + 1) * h
+        X, Y, W = np.meshgrid(r, r, r, indexing="ij")
+        rr = np.sqrt(X ** 2 + Y ** 2 + W ** 2)
+        mask = rr > 0
+        S = h ** 3 * np.sum(np.exp(-rr[mask] ** 2 / s ** 2) / rr[mask])
+        coef.append((S - 2 * np.pi * s * s) / h ** 2)
+    # Richardson: the O(h^2) remainder of the coefficient is removed
+    extrap = (4 * coef[1] - coef[0]) / 3
+    assert abs(extrap - Zc) < 1e-4
+    assert abs(Zc - (-2.8372974794806)) < 1e-10
+
+
+# --------------------------------------------------------------- entries
+
+def test_kernel_entries_symmetries():
+    """G is even in every offset, G^d odd in t_d and even in the others; axes permute."""
+    n, k = 6, 5.0
+    E = oracle.kernel_entries(n, k)
+    G, G1, G2, G3 = E
+    assert np.allclose(G, G[::-1, :, :]) and np.allclose(G, G[:, ::-1, :]) and np.allclose(G, G[:, :, ::-1])
+    assert np.allclose(G1, -G1[:, :, ::-1]) and np.allclose(G1, G1[::-1, :, :])
+    assert np.allclose(G3, -G3[::-1, :, :]) and np.allclose(G3, G3[:, :, ::-1])
+    # array axes are [t3][t2][t1]: swapping t1 and t2 maps G1 to G2
+    assert np.allclose(G2, np.transpose(G1, (0, 2, 1)))
+    assert np.allclose(G, np.transpose(G, (0, 2, 1)))
+
+
+@pytest.mark.parametrize("quad,expected", [(oracle.QUAD_ORDER4, 4.0), (oracle.QUAD_ORDER2, 2.0)])
+def test_convergence_order_against_closed_form(quad, expected):
+    """The corrected quadrature is fourth order (Section 2); uncorrected is second.
+
+    G*rho and G^d*rho of a radial C-infinity bump have the closed form of the
+    Helmholtz addition theorem (oracle/radial.py); the discrete convolution is
+    compared at common nodes for h = 1/16, 1/32, 1/64.
+    """
+    k = 2 * np.pi
+    pts_idx = [3, 5, 8, 11, 13]
+    pts = np.array([(a / 16, b / 16, c / 16) for c in pts_idx for b in pts_idx for a in pts_idx])
+    exact = radial.exact_on_points(pts, k)
+    errs = []
+    for M in (16, 32, 64):
+        n = M - 1
+        rho = radial.bump_on_grid(n)
+        s = M // 16
+        e = []
+        for w in range(4):
+            conv = oracle.convolve(n, k, w, rho, quad)
+            vals = np.array([conv[c * s - 1, b * s - 1, a * s - 1] for c in pts_idx for b in pts_idx for a in pts_idx])
+            e.append(np.max(np.abs(vals - exact[w])) / np.max(np.abs(exact[w])))
+        errs.append(e)
+    errs = np.array(errs)
+    orders = np.log2(errs[:-1] / errs[1:])
+    assert np.all(orders > expected - 0.3), orders
+    assert np.all(orders < expected + 0.6), orders
+
+
+# --------------------------------------------------------------- operator
+
+def _medium(n, seed=3):
+    eps, grad = si.random_medium(n, seed)
+    return oracle.medium(eps, grad)
+
+
+def test_identity_in_vacuum():
+    """eps == 1 gives m = 0 and p = 0, so A = I exactly (Eq. discrete_block)."""
+    n = 6
+    eps = np.ones((n, n, n), np.complex128)
+    grad = np.zeros((3, n, n, n), np.complex128)
+    m, p = oracle.medium(eps, grad)
+    x = si.random_field(n, 1)
+    assert np.array_equal(oracle.apply_fft(n, 3.0, m, p, x), x)
+    assert np.array_equal(oracle.apply_direct(n, 3.0, m, p, x), x)
+
+
+@pytest.mark.parametrize("n", [4, 5, 7, 8])
+def test_direct_sum_equals_fft_apply(n):
+    """O(N^2) summation of Eq. (discrete) equals the circulant-embedded FFT apply."""
+    k = 2.5 * n / 4
+    m, p = _medium(n, seed=n)
+    x = si.random_field(n, 10 + n)
+    yd = oracle.apply_direct(n, k, m, p, x)
+    yf = oracle.apply_fft(n, k, m, p, x)
+    assert np.linalg.norm(yd - yf) / np.linalg.norm(yd) < 1e-13
+
+
+def test_contrast_and_gradient_weights():
+    """m = 1 - eps and p^d = (d_d m)/(1 - m), checked by complex-step-free algebra."""
+    n = 5
+    eps, grad = si.random_medium(n, 4)
+    m, p = oracle.medium(eps, grad)
+    assert np.allclose(m, 1 - eps)
+    dm = -grad
+    assert np.allclose(p * (1 - m)[None], dm)
+
+
+def test_toeplitz_reciprocity():
+    """u^T (G*v) = v^T (G*u) and u^T (G^d*v) = -v^T (G^d*u) (even and odd kernels)."""
+    n, k = 9, 4.0
+    u = si.random_field(n, 5)[0]
+    v = si.random_field(n, 6)[0]
+    a = np.sum(u * oracle.convolve(n, k, 0, v))
+    b = np.sum(v * oracle.convolve(n, k, 0, u))
+    assert abs(a - b) < 1e-13 * abs(a)
+    for d in (1, 2, 3):
+        a = np.sum(u * oracle.convolve(n, k, d, v))
+        b = np.sum(v * oracle.convolve(n, k, d, u))
+        assert abs(a + b) < 1e-12 * abs(a)
+
+
+def test_dense_matches_direct_apply():
+    n, k = 4, 2.0
+    m, p = _medium(n)
+    A = oracle.dense_A(n, k, m, p)
+    x = si.random_field(n, 7)
+    assert np.allclose(A @ x.ravel(), oracle.apply_direct(n, k, m, p, x).ravel(), rtol=0, atol=1e-12)
+
+
+# --------------------------------------------------------------- stencils
+
+def _explicit_M(n, k, cls):
+    """M of the paper's minimisation, built here from the entries table by brute force."""
+    E = oracle.kernel_entries(n, k)
+    tau = oracle.class_tau(cls)
+    c = [cls % 3, (cls // 3) % 3, cls // 9]
+    rng = {0: (0, n - 1), 1: (-(n - 2), n - 2), 2: (-(n - 1), 0)}
+    taus = set(map(tuple, tau.tolist()))
+    comp = [(u1, u2, u3)
+            for u3 in range(rng[c[2]][0], rng[c[2]][1] + 1)
+            for u2 in range(rng[c[1]][0], rng[c[1]][1] + 1)
+            for u1 in range(rng[c[0]][0], rng[c[0]][1] + 1)
+            if (u1, u2, u3) not in taus]
+    T, U = len(tau), len(comp)
+    M = np.zeros((3 * T, 4 * U), np.complex128)
+    off = n - 1
+    for oi, o in enumerate(tau):
+        for ui, u in enumerate(comp):
+            t = (o[0] - u[0], o[1] - u[1], o[2] - u[2])
+            g = E[:, t[2] + off, t[1] + off, t[0] + off]
+            for d in range(3):
+                M[d * T + oi, d * U + ui] = k * k * g[0]
+                M[d * T + oi, 3 * U + ui] = g[1 + d]
+    return M
+
+
+@pytest.mark.parametrize("cls", [13, 12, 4, 0, 26, 22])
+def test_stencil_is_min_annihilator(cls):
+    """alpha = conj(3 smallest left singular vectors of M): ||alpha^T M||_F equals the
+    root-sum-square of the 3 smallest singular values, alpha^H alpha = I, and the
+    subspace equals the one from a library SVD of the explicitly formed M."""
+    n, k = 7, 2 * np.pi * 7 / 8
+    alpha, beta, sv = oracle.class_stencil(n, k, cls)
+    M = _explicit_M(n, k, cls)
+    U, S, _ = np.linalg.svd(M, full_matrices=False)
+    order = np.argsort(S)
+    assert np.allclose(np.sort(S), sv, rtol=1e-9, atol=1e-14 * S.max())
+    assert np.allclose(alpha.conj().T @ alpha, np.eye(3), atol=1e-12)
+    res = np.linalg.norm(alpha.T @ M)
+    assert abs(res - np.sqrt(np.sum(sv[:3] ** 2))) < 1e-9 * res + 1e-15
+    U3 = U[:, order[:3]]
+    P_lib = U3 @ U3.conj().T
+    P_or = alpha.conj() @ alpha.T
+    gap = sv[3] / sv[2]
+    assert np.linalg.norm(P_lib - P_or) < 1e-8 / max(gap - 1, 1e-3)
+
+
+def test_stencil_beats_gamma_ansatz_and_per_point_svd():
+    """The class minimiser is no worse than the Helmholtz-stencil ansatz
+    alpha = diag(gamma,gamma,gamma) (Eq. alphagamma), and a per-point SVD over the
+    true complement tau_i^c (a subset of the class complement) is no worse than
+    the class stencil (translation-invariance argument of Section 3.2)."""
+    n, k = 8, 2 * np.pi
+    cls = 13
+    alpha, beta, sv = oracle.class_stencil(n, k, cls)
+    M = _explicit_M(n, k, cls)
+    T = 27
+    U = M.shape[1] // 4
+    # gamma ansatz: best unit gamma for the weighted scalar problem
+    blocks = M[:T, :U] / (k * k)
+    G1, G2, G3 = M[:T, 3 * U:], M[T:2 * T, 3 * U:], M[2 * T:, 3 * U:]
+    H = 3 * k ** 4 * blocks @ blocks.conj().T + G1 @ G1.conj().T + G2 @ G2.conj().T + G3 @ G3.conj().T
+    w, V = np.linalg.eigh(H)
+    gamma = V[:, 0].conj()
+    ag = np.zeros((3 * T, 3), np.complex128)
+    for d in range(3):
+        ag[d * T:(d + 1) * T, d] = gamma / np.sqrt(1.0)
+    ansatz = np.linalg.norm(ag.T @ M)
+    best = np.linalg.norm(alpha.T @ M)
+    assert best <= ansatz * (1 + 1e-12)
+    # per-point: interior point i = (2,2,2) (1-based) has complement offsets in [-1, n-2]^3
+    Mfull = M
+    taus = set(map(tuple, oracle.class_tau(cls).tolist()))
+    comp = [(u1, u2, u3) for u3 in range(-(n - 2), n - 1) for u2 in range(-(n - 2), n - 1)
+            for u1 in range(-(n - 2), n - 1) if (u1, u2, u3) not in taus]
+    keep = [ui for ui, u in enumerate(comp) if all(-1 <= x <= n - 2 for x in u)]
+    cols = np.concatenate([np.array(keep) + f * U for f in range(4)])
+    Msub = Mfull[:, cols]
+    s_sub = np.sort(np.linalg.svd(Msub, compute_uv=False))
+    assert np.sqrt(np.sum(s_sub[:3] ** 2)) <= np.sqrt(np.sum(sv[:3] ** 2)) * (1 + 1e-12)
+
+
+def _reflect_class(cls, d):
+    c = [cls % 3, (cls // 3) % 3, cls // 9]
+    c[d] = 2 - c[d]
+    return c[0] + 3 * c[1] + 9 * c[2]
+
+
+def test_mirrored_classes_are_reflections():
+    """A reflection x_d -> -x_d maps G to G and G^d to -G^d, so the stencil of the
+    mirrored boundary class is the reflected stencil with component d negated."""
+    n, k = 7, 4.0
+    for cls, d in [(12, 0), (4, 1), (0, 2), (10, 0)]:
+        cm = _reflect_class(cls, d)
+        a, _, sv = oracle.class_stencil(n, k, cls)
+        am, _, svm = oracle.class_stencil(n, k, cm)
+        assert np.allclose(sv, svm, rtol=1e-10)
+        tau = oracle.class_tau(cls)
+        taum = oracle.class_tau(cm)
+        T = len(tau)
+        mapped = np.zeros_like(a)
+        index_m = {tuple(o): i for i, o in enumerate(taum.tolist())}
+        for oi, o in enumerate(tau.tolist()):
+            o2 = list(o)
+            o2[d] = -o2[d]
+            j = index_m[tuple(o2)]
+            for e in range(3):
+                sgn = -1.0 if e == d else 1.0
+                mapped[e * T + j] = sgn * a[e * T + oi]
+        P1 = mapped.conj() @ mapped.T
+        P2 = am.conj() @ am.T
+        assert np.linalg.norm(P1 - P2) < 1e-8
+
+
+def test_sparse_rows_equal_QA_on_pattern():
+    """Inside the neighbourhood pattern the rows of Q A equal S exactly
+    (Eqs. nbr_i_block_alpha, alphabeta, nbr_i_block_alpha_approx); off the pattern
+    they are alpha^T of the dropped block times the medium."""
+    n, k = 5, 3.0
+    m, p = _medium(n, seed=11)
+    A = oracle.dense_A(n, k, m, p)
+    al, be, svs = oracle.all_stencils(n, k)
+    S = oracle.dense_S(n, m, p, al, be)
+    N3 = 3 * n ** 3
+    QA = np.zeros((N3, N3), np.complex128)
+    for col in range(N3):
+        QA[:, col] = oracle.apply_Q(n, al, A[:, col].reshape(3, n, n, n)).ravel()
+    pattern = S != 0
+    assert np.max(np.abs((QA - S)[pattern])) < 1e-12 * np.max(np.abs(QA))
+    # the dropped part is small relative to the kept part
+    assert np.linalg.norm(QA[~pattern]) < 0.5 * np.linalg.norm(QA[pattern])
+
+
+def test_apply_Q_matches_brute_force():
+    n = 4
+    al = si.random_field(1, 9, 27 * 81 * 3 // 3).reshape(-1)[: 27 * 81 * 3].reshape(27, 81, 3)
+    v = si.random_field(n, 12)
+    y = oracle.apply_Q(n, al, v)
+    i = (0, 1, 3)  # (i1, i2, i3) 0-based: face/low-face/high-face point
+    c = [0, 1, 2]
+    cls = c[0] + 3 * c[1] + 9 * c[2]
+    tau = oracle.class_tau(cls)
+    T = len(tau)
+    for comp in range(3):
+        s = 0
+        for d in range(3):
+            for oi, o in enumerate(tau):
+                s += al[cls, d * T + oi, comp] * v[d, i[2] + o[2], i[1] + o[1], i[0] + o[0]]
+        assert abs(y[comp, i[2], i[1], i[0]] - s) < 1e-12
+
+
+# --------------------------------------------------------------- solves
+
+def test_banded_S_solve_matches_library_solve():
+    n, k = 5, 3.0
+    m, p = _medium(n, seed=2)
+    al, be, _ = oracle.all_stencils(n, k)
+    S = oracle.dense_S(n, m, p, al, be)
+    b = si.random_field(n, 3)
+    f = oracle.SFactor(n, m, p, al, be)
+    x = f.solve(b)
+    xr = np.linalg.solve(S, b.ravel())
+    assert np.linalg.norm(x.ravel() - xr) / np.linalg.norm(xr) < 1e-10
+
+
+def test_gmres_matches_dense_lu_and_library():
+    n = 5
+    k = si.wavenumber_for_grid(n)
+    eps, grad = si.medium_gaussian(n)
+    m, p = oracle.medium(eps, grad)
+    einc = si.plane_wave(n, k, (0, 0, 1), (1, 0, 0))
+    g = einc - oracle.apply_fft(n, k, m, p, einc)
+    A = oracle.dense_A(n, k, m, p)
+    x_lu = oracle.dense_solve(A, g.ravel())
+    x_np = np.linalg.solve(A, g.ravel())
+    assert np.linalg.norm(x_lu - x_np) / np.linalg.norm(x_np) < 1e-12
+    x, it, rel, _ = oracle.gmres(n, k, m, p, g, tol=1e-13)
+    assert rel < 1e-13
+    assert np.linalg.norm(x.ravel() - x_np) / np.linalg.norm(x_np) < 1e-10
+
+
+def test_born_limit():
+    """Scaling the contrast by s gives E^s = g + O(s^2 ...): ||E^s - g||/||g|| = O(s)."""
+    n = 6
+    k = si.wavenumber_for_grid(n)
+    eps, grad = si.medium_gaussian(n)
+    einc = si.plane_wave(n, k, (0, 0, 1), (1, 0, 0))
+    ratios = []
+    for s in (1e-2, 5e-3):
+        m, p = oracle.medium(1 + s * (eps - 1), s * grad)
+        g = einc - oracle.apply_fft(n, k, m, p, einc)
+        x, _, rel, _ = oracle.gmres(n, k, m, p, g, tol=1e-13)
+        ratios.append(np.linalg.norm(x - g) / np.linalg.norm(g))
+    assert 1.7 < ratios[0] / ratios[1] < 2.3
+
+
+def test_preconditioner_cuts_iterations():
+    """Behaviour (parity unpinned): S^{-1}Q-preconditioned GMRES needs few iterations
+    (the paper reports fewer than ten in every case; tests/golden/paper_iteration_counts.txt)."""
+    n = 10
+    k = si.wavenumber_for_grid(n)
+    eps, grad = si.medium_gaussian(n)
+    m, p = oracle.medium(eps, grad)
+    einc = si.plane_wave(n, k, (0, 0, 1), (1, 0, 0))
+    g = einc - oracle.apply_fft(n, k, m, p, einc)
+    al, be, _ = oracle.all_stencils(n, k)
+    f = oracle.SFactor(n, m, p, al, be)
+    x, it_p, rel_p, _ = oracle.gmres(n, k, m, p, g, tol=1e-6, restart=20, maxit=200, sfactor=f, alpha_all=al)
+    x0, it_0, rel_0, _ = oracle.gmres(n, k, m, p, g, tol=1e-6, restart=20, maxit=400)
+    assert rel_p <= 1e-6
+    assert it_p < it_0
+    assert it_p <= 12
+    # the preconditioned solution solves the original system too
+    r = g - oracle.apply_fft(n, k, m, p, x)
+    assert np.linalg.norm(r) / np.linalg.norm(g) < 1e-4
