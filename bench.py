@@ -1,0 +1,314 @@
+"""Benchmark of the operator apply on GB300 (one JSON line on rank 0).
+
+Default workload (``n64_bumps8``): n = 64 grid (262,144 points, 786,432 complex
+unknowns), k = 16 pi (8 wavelengths at about 8 points per wavelength), eps = 1 +
+tapered sum of 8 seeded Gaussian bumps, one incident plane wave, complex64.
+One step = one application of the operator on the hot path (``--op QA``: Q A,
+the sparsifying row combination after A; ``--op A``: A alone).
+
+Timing: W warm-up steps, then K steps, each bracketed by CUDA events on the
+launch stream, with an L2 flush (a 512 MiB buffer write) between steps, barrier
+and synchronize around the timed region, max over ranks.  ``e2e`` repeats the
+measurement through the public API with the input copied from pinned host
+memory and the result read back every step.  ``cpu_baseline`` times the FP64
+CPU oracle's FFT apply on a bounded sample on the host cores.
+
+``--impl reference``: the CPU oracle timed as it stands (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import spm_inputs as si  # noqa: E402
+
+METRIC = "operator applies/s + HBM GB/s frac; time-to-1e-6 solve, cx64-mixed vs FP64"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="n64_bumps8")
+    ap.add_argument("--prec", default="c64", choices=["c64", "c128"])
+    ap.add_argument("--op", default="A", choices=["A", "QA"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def compulsory_bytes(n, prec, nrhs=1):
+    """Algorithmic bytes of one apply: read x, m, p (complex) and the 4 octant
+    spectra, write y.  Each complex element is 8 (c64) or 16 (c128) bytes."""
+    el = 8 if prec == "c64" else 16
+    N = n ** 3
+    return el * (nrhs * 3 * N + N + 3 * N + 4 * (n + 1) ** 3 + nrhs * 3 * N)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def wait_first(self, timeout=10.0):
+        t0 = time.time()
+        while self.proc is not None and not self.lines and time.time() - t0 < timeout:
+            time.sleep(0.05)
+
+    def mark(self):
+        return len(self.lines)
+
+    def stop(self, begin=0, end=None):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines[begin:end]:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(wl, seconds, op):
+    """FP64 oracle FFT apply on a bounded sample (whole applies until ~seconds)."""
+    import oracle
+    n, k = wl["n"], wl["omega"]
+    m, p = oracle.medium(wl["eps"], wl["grad"])
+    x = wl["einc"][0]
+    F = oracle.FFTOperator(n, k)
+    F.apply(m, p, x)  # warm
+    t0 = time.perf_counter()
+    count = 0
+    while True:
+        F.apply(m, p, x)
+        count += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    F.close()
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": count / dt, "unit": "applies/s", "cores": cores, "kind": "oracle",
+            "sample": f"{count} FP64 FFT applies of A (oracle, spectra precomputed) at n={n}; "
+                      f"apply {op} on the GPU side"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    wl = si.workload(args.workload)
+    cb = cpu_baseline(wl, args.cpu_seconds, args.op)
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "applies/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 / cb["value"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": {"workload": args.workload, "n": wl["n"], "nrhs": 1, "op": "A"},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "applies/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("apply.cu", "fft.cuh", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1804_02297_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload, prec, op):
+    """DRAM bytes per apply from the committed ncu summary, if the kernels are unchanged."""
+    path = os.path.join(ROOT, "profiles", "apply_traffic.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    e = d.get(f"{workload}/{prec}/{op}")
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_apply")
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import paper_1804_02297_gb300 as spm
+
+    wl = si.workload(args.workload)
+    n = wl["n"]
+    P = spm.Problem(n, wl["omega"], wl["eps"], wl["grad"])
+    dtype = torch.complex64 if args.prec == "c64" else torch.complex128
+    x = torch.from_numpy(wl["einc"][0]).to(dtype).to("cuda").contiguous()
+    y = torch.zeros_like(x)
+    if args.op == "QA":
+        P.build_stencils(spm.SPM_C64)
+        fn = P.apply_QA
+        launches_per_step = 6
+    else:
+        fn = P.apply_A
+        launches_per_step = 5
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    for _ in range(args.warmup):
+        fn(x, y)
+    torch.cuda.synchronize()
+    sampler.wait_first()
+    if world > 1:
+        torch.distributed.barrier()
+    mark0 = sampler.mark()
+    times = []
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn(x, y)
+        e1.record(stream)
+        times.append((e0, e1))
+    torch.cuda.synchronize()
+    mark1 = sampler.mark()
+    time.sleep(0.25)
+    clocks = sampler.stop(max(0, mark0 - 1), mark1 + 1)
+    step_ms = [a.elapsed_time(b) for a, b in times]
+    total_ms = float(np.sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * args.steps / (total_ms / 1000.0)
+
+    # e2e: pinned host input -> device -> apply -> host, every step
+    xh = torch.from_numpy(wl["einc"][0]).to(dtype).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    xd = torch.empty_like(x)
+    for _ in range(2):
+        xd.copy_(xh, non_blocking=True)
+        fn(xd, y)
+        yh.copy_(y, non_blocking=True)
+    torch.cuda.synchronize()
+    ev = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        xd.copy_(xh, non_blocking=True)
+        fn(xd, y)
+        yh.copy_(y, non_blocking=True)
+        e1.record(stream)
+        ev.append((e0, e1))
+    torch.cuda.synchronize()
+    e2e_ms = float(np.sum([a.elapsed_time(b) for a, b in ev]))
+    if world > 1:
+        t = torch.tensor([e2e_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    nbytes = xh.numel() * xh.element_size()
+
+    peak, peak_kind = peaks()
+    alg = compulsory_bytes(n, args.prec)
+    achieved = alg / (ms_per_step / 1000.0) / 1e9
+    roof = {"bound": "hbm", "kernel": f"apply_{args.op} ({launches_per_step} launches)",
+            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_source": peak_kind, "algorithmic_bytes": alg,
+            "traffic": recorded_traffic(args.workload, args.prec, args.op)}
+
+    line = {"metric": METRIC, "value": value, "unit": "applies/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
+            "config": {"workload": args.workload, "n": n, "nrhs": 1, "op": args.op, "l2": "flushed (512 MiB write) between steps",
+                       "parallelism": f"replicas{world}"},
+            "roofline": roof,
+            "e2e": {"value": world * args.steps / (e2e_ms / 1000.0), "unit": "applies/s",
+                    "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clocks,
+            "step_ms_min": float(np.min(step_ms)), "step_ms_median": float(np.median(step_ms))}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds, args.op)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,191 @@
+/*
+ * spm.h -- C ABI of libspm, a GB300 (sm_103a) implementation of the hot path of
+ * the sparsifying preconditioner for the 3-D time-harmonic Maxwell volume
+ * integral equation (F. Liu and L. Ying, "Sparsifying preconditioner for the
+ * time-harmonic Maxwell's equations").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid (Section 2): Omega = (0,1)^3, n points per dimension, h = 1/(n+1), node
+ *   i = (i1,i2,i3), 1 <= i_d <= n, at x = i*h.  Grid arrays are [i3][i2][i1]
+ *   with i1 fastest.
+ * Fields: a vector field is [d][i3][i2][i1], d = 0,1,2 (the paper's E^1,E^2,E^3);
+ *   nrhs fields are stacked outermost: [b][d][i3][i2][i1].  Complex numbers are
+ *   interleaved (re, im).  SPM_C128 buffers hold double pairs, SPM_C64 buffers
+ *   float pairs.
+ * Memory: arguments named *_host are host pointers, *_dev device pointers.  The
+ *   caller owns every buffer it passes; the library owns everything inside an
+ *   spm_problem (spectra, stencils, sparse factor, workspaces) until
+ *   spm_destroy.  Input and output buffers of one call must not alias.
+ * Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  Device
+ *   work is enqueued on it and the call returns without synchronising, except
+ *   where stated (set-up calls and spm_solve synchronise).
+ * Errors: every function returns spm_status (0 = SPM_OK) and never throws or
+ *   aborts; spm_last_error() gives a thread-local message for the last failure.
+ *   A handle must not be used from two host threads at once.
+ */
+#ifndef SPM_H
+#define SPM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct spm_problem_s *spm_problem;
+
+typedef enum {
+    SPM_OK = 0,
+    SPM_ERR_INVALID_ARG = 1,    /* bad size, pointer or enum value */
+    SPM_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+    SPM_ERR_OOM = 3,            /* device allocation failed */
+    SPM_ERR_NOT_BUILT = 4,      /* stencils or factor requested before they exist */
+    SPM_ERR_NO_CONVERGENCE = 5, /* solver hit maxit; x holds the last iterate */
+    SPM_ERR_TIMEOUT = 6,        /* a bounded device wait gave up */
+    SPM_ERR_NUMERICAL = 7       /* zero pivot, NaN or Inf */
+} spm_status;
+
+/* Quadrature for the Toeplitz entries near the diagonal (Section 2, the
+ * "fourth-order quadrature correction" after Eq. discrete).  ORDER4: corrected
+ * trapezoidal rule, G_0 = h^2 (i k h - Z)/(4 pi) and G^d at t = +-e_d shifted by
+ * +-h Z/(24 pi), Z = sum'_{j in Z^3} |j|^{-1} (continued) = -2.8372974794806...
+ * ORDER2: punctured trapezoidal rule, G_0 = h^3 i k/(4 pi), no other change. */
+typedef enum { SPM_QUAD_ORDER4 = 0, SPM_QUAD_ORDER2 = 1 } spm_quad;
+
+/* Arithmetic of a call: complex128, complex64 (FP32 accumulation), or, for
+ * spm_solve only, complex64 inner iterations inside an FP64 outer loop. */
+typedef enum { SPM_C128 = 0, SPM_C64 = 1, SPM_MIXED = 2 } spm_prec;
+
+/* ---------------------------------------------------------------- set-up */
+
+/* Create a problem on an n^3 grid (Section 2).  omega is the normalised
+ * frequency; with eps0 = mu0 = 1 the wavenumber is k = omega.
+ * eps_host: n^3 complex doubles, the relative permittivity eps + i sigma/omega
+ *   at the nodes; eps - 1 must vanish smoothly at the boundary of Omega (the
+ *   contrast m = 1 - eps is compactly supported, Section 2).
+ * grad_eps_host: 3 n^3 complex doubles [d][i3][i2][i1], the gradient of eps, or
+ *   NULL to use fourth-order central differences with eps = 1 outside the grid.
+ * The library forms m = 1 - eps and p^d = (d_d m)/(1 - m) = -d_d eps/eps
+ * (Section 2, definitions before Eq. discrete), the four Toeplitz kernels
+ * G, G^1, G^2, G^3 and their spectra on a 2n-periodic grid (circulant embedding;
+ * FP64, stored in complex128 and complex64).  n must be in [4, 512].
+ * Synchronises `stream`.  On success *out is a new handle. */
+spm_status spm_create_problem(int n, double omega, const double *eps_host,
+                              const double *grad_eps_host, spm_quad quad,
+                              void *stream, spm_problem *out);
+
+/* Release every device and host resource of the handle. NULL is accepted. */
+spm_status spm_destroy(spm_problem prob);
+
+/* Grid size n, wavenumber k and unknown count 3 n^3 of a handle. */
+spm_status spm_problem_info(spm_problem prob, int *n, double *k, long long *unknowns);
+
+/* ---------------------------------------------------------- operator A */
+
+/* y = A x, A = I + [k^2 G, G^d] [m; p] (Eq. discrete_block), for nrhs fields.
+ * x_dev, y_dev: nrhs x 3 x n^3 complex in `prec` (SPM_C128 or SPM_C64).
+ * Evaluated matrix-free by zero-padded FFT convolution with the four kernel
+ * spectra (Section 2: the convolutions "can be evaluated efficiently by the
+ * FFT").  Uses library-owned workspace sized for the largest nrhs seen. */
+spm_status spm_apply_A(spm_problem prob, spm_prec prec, const void *x_dev, void *y_dev,
+                       int nrhs, void *stream);
+
+/* y = Q A x: A as above followed by the sparsifying row combination Q,
+ * (Q v)_{i,c} = sum_{(d,o) in tau(class i)} alpha_class[(d,o),c] v^d_{i+o}
+ * (Eq. nbr_i_block_alpha; classes of Section 3.2).  Needs stencils
+ * (spm_build_stencils or spm_set_stencils), else SPM_ERR_NOT_BUILT. */
+spm_status spm_apply_QA(spm_problem prob, spm_prec prec, const void *x_dev, void *y_dev,
+                        int nrhs, void *stream);
+
+/* y = Q v (the row combination alone), same layout and requirements. */
+spm_status spm_apply_Q(spm_problem prob, spm_prec prec, const void *v_dev, void *y_dev,
+                       int nrhs, void *stream);
+
+/* ----------------------------------------------------------- stencils */
+
+/* Point classes (Section 3.2): class = c1 + 3 c2 + 9 c3 with c_d = 0 if i_d = 1,
+ * 2 if i_d = n, else 1.  The neighbourhood offsets o of a class are, per
+ * dimension, {0,1}, {-1,0,1} or {-1,0}; T = |tau| is 27, 18, 12 or 8; offsets
+ * are enumerated o3 outer, o2, o1 inner, each ascending.  Stencil tables are
+ * packed for all 27 classes:
+ *   alpha: [27][81][3] complex double, row (d,o) = d*T + o (rows >= 3T unused),
+ *          alpha = conj(the three left singular vectors of M with the smallest
+ *          singular values), M the off-neighbourhood block (Section 3.1,
+ *          the minimisation of ||alpha^T M||_F with alpha^T alpha = I);
+ *   beta:  [27][108][3] complex double, row (f,o) = f*T + o, beta = B^T alpha
+ *          with B the in-neighbourhood block (Eq. alphabeta);
+ *   sv:    [27][81] double, the 3T singular values of M, ascending.          */
+
+/* Compute alpha, beta for all classes on the device (FP64), assemble the
+ * sparse matrix S (Eq. nbr_i_block_alpha_approx with "~" replaced by "="),
+ * and factor it by nested dissection in `factor_prec` (SPM_C128 or SPM_C64).
+ * Synchronises the problem's creation stream. */
+spm_status spm_build_stencils(spm_problem prob, spm_prec factor_prec);
+
+/* Install caller-computed stencil tables (layout above, host memory), then
+ * assemble S.  The factor is dropped; spm_factor_S builds it again. */
+spm_status spm_set_stencils(spm_problem prob, const double *alpha_host, const double *beta_host);
+
+/* Copy the current stencil tables to host memory; any pointer may be NULL. */
+spm_status spm_get_stencils(spm_problem prob, double *alpha_host, double *beta_host, double *sv_host);
+
+/* Factor the assembled S (nested dissection, multifrontal LU on the device) in
+ * `prec` (SPM_C128 or SPM_C64).  Synchronises. */
+spm_status spm_factor_S(spm_problem prob, spm_prec prec);
+
+/* y = S x for nrhs fields (sparse product with the assembled S). */
+spm_status spm_apply_S(spm_problem prob, spm_prec prec, const void *x_dev, void *y_dev,
+                       int nrhs, void *stream);
+
+/* x = S^{-1} b with the factor of matching precision (forward and backward
+ * substitution through the elimination tree). */
+spm_status spm_solve_S(spm_problem prob, spm_prec prec, const void *b_dev, void *x_dev,
+                       int nrhs, void *stream);
+
+/* ------------------------------------------------------------- solving */
+
+typedef struct {
+    int iterations;         /* preconditioned GMRES iterations, summed over RHS and restarts */
+    int outer_steps;        /* FP64 outer refinement steps (SPM_MIXED), else restarts */
+    double true_relres;     /* max over RHS of ||g - A x|| / ||g|| in FP64 at exit */
+    double solve_ms;        /* wall time of the call */
+} spm_solve_info;
+
+/* Incident plane waves E^i = pol_b exp(i k dir_b . x) (Section 4), nrhs of them.
+ * dir_host, pol_host: nrhs x 3 doubles.  e_dev: nrhs x 3 x n^3 in `prec`. */
+spm_status spm_incident_plane_wave(spm_problem prob, spm_prec prec, const double *dir_host,
+                                   const double *pol_host, int nrhs, void *e_dev, void *stream);
+
+/* Right-hand side of Eq. (scattter): g = E^i - A E^i (since
+ * (A - I) E^i = k^2 G*(m E^i) + grad G*(p.E^i) = -g).  complex128 buffers. */
+spm_status spm_rhs_from_incident(spm_problem prob, const void *einc_dev, void *g_dev, int nrhs,
+                                 void *stream);
+
+/* Solve A x = g (Eq. discrete_block) for nrhs right-hand sides by GMRES(restart)
+ * left-preconditioned with S^{-1} Q (Section 3.1, last paragraph), stopping
+ * when every FP64 true relative residual ||g - A x||/||g|| <= tol.
+ * prec: SPM_C128 (everything FP64), SPM_C64 or SPM_MIXED (complex64 operator
+ * and factor inside FP64 iterative refinement with FP64 residuals).
+ * g_dev, x_dev: complex128, nrhs x 3 x n^3; x_dev is the initial guess on entry.
+ * restart <= 0 selects 20 (Section 4).  Returns SPM_ERR_NO_CONVERGENCE with the
+ * last iterate in x_dev if maxit inner iterations per RHS are exceeded.
+ * Synchronises. */
+spm_status spm_solve(spm_problem prob, spm_prec prec, const void *g_dev, void *x_dev, int nrhs,
+                     double tol, int maxit, int restart, spm_solve_info *info);
+
+/* -------------------------------------------------------- inspection */
+
+/* The library's Toeplitz entries for offsets t in [-(n-1), n-1]^3,
+ * out_host: 4 x (2n-1)^3 complex doubles [kern][t3][t2][t1], kern = G,G^1,G^2,G^3
+ * (Section 2).  Evaluated on the device in FP64. */
+spm_status spm_kernel_entries(spm_problem prob, double *out_host);
+
+/* The lattice constant Z used by SPM_QUAD_ORDER4 (computed by Ewald summation). */
+double spm_lattice_constant(void);
+
+/* Thread-local message of the last failing call ("" if none). */
+const char *spm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPM_H */

@@ -1,0 +1,225 @@
+"""Python binding of libspm (include/spm.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts numpy/torch
+arguments to pointers and status codes to exceptions.  Importing it loads
+``_build/libspm.so`` and raises ImportError if the library has not been built
+(``python paper_1804_02297_gb300/build.py``); there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libspm.so")
+
+SPM_OK, SPM_ERR_INVALID_ARG, SPM_ERR_CUDA, SPM_ERR_OOM, SPM_ERR_NOT_BUILT, SPM_ERR_NO_CONVERGENCE, \
+    SPM_ERR_TIMEOUT, SPM_ERR_NUMERICAL = range(8)
+SPM_QUAD_ORDER4, SPM_QUAD_ORDER2 = 0, 1
+SPM_C128, SPM_C64, SPM_MIXED = 0, 1, 2
+
+# every symbol include/spm.h declares
+EXPORTS = [
+    "spm_create_problem", "spm_destroy", "spm_problem_info", "spm_apply_A", "spm_apply_QA", "spm_apply_Q",
+    "spm_build_stencils", "spm_set_stencils", "spm_get_stencils", "spm_factor_S", "spm_apply_S",
+    "spm_solve_S", "spm_incident_plane_wave", "spm_rhs_from_incident", "spm_solve", "spm_kernel_entries",
+    "spm_lattice_constant", "spm_last_error",
+]
+
+
+class SpmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"libspm status {status}: {msg}")
+        self.status = status
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("outer_steps", ctypes.c_int),
+                ("true_relres", ctypes.c_double), ("solve_ms", ctypes.c_double)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libspm.so not built at {LIB_PATH}; run paper_1804_02297_gb300/build.py")
+    L = ctypes.CDLL(LIB_PATH)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "spm_create_problem": [I, D, P, P, I, P, ctypes.POINTER(P)],
+        "spm_destroy": [P],
+        "spm_problem_info": [P, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)],
+        "spm_apply_A": [P, I, P, P, I, P],
+        "spm_apply_QA": [P, I, P, P, I, P],
+        "spm_apply_Q": [P, I, P, P, I, P],
+        "spm_build_stencils": [P, I],
+        "spm_set_stencils": [P, P, P],
+        "spm_get_stencils": [P, P, P, P],
+        "spm_factor_S": [P, I],
+        "spm_apply_S": [P, I, P, P, I, P],
+        "spm_solve_S": [P, I, P, P, I, P],
+        "spm_incident_plane_wave": [P, I, P, P, I, P, P],
+        "spm_rhs_from_incident": [P, P, P, I, P],
+        "spm_solve": [P, I, P, P, I, D, I, I, ctypes.POINTER(SolveInfo)],
+        "spm_kernel_entries": [P, P],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = I
+    L.spm_lattice_constant.restype = D
+    L.spm_lattice_constant.argtypes = []
+    L.spm_last_error.restype = ctypes.c_char_p
+    L.spm_last_error.argtypes = []
+    return L
+
+
+lib = _load()
+
+
+def _check(status):
+    if status != SPM_OK:
+        raise SpmError(status, lib.spm_last_error().decode())
+    return status
+
+
+def _ptr(a):
+    """Device pointer of a torch tensor or host pointer of a numpy array."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(a.data_ptr())
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _prec_of(t):
+    s = str(t.dtype)
+    if s.endswith("complex128"):
+        return SPM_C128
+    if s.endswith("complex64"):
+        return SPM_C64
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except Exception:
+            return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _nrhs(x, n):
+    return x.numel() // (3 * n ** 3)
+
+
+def spm_lattice_constant() -> float:
+    return lib.spm_lattice_constant()
+
+
+class Problem:
+    """Owns one spm_problem handle (spm_create_problem ... spm_destroy)."""
+
+    def __init__(self, n, omega, eps, grad_eps=None, quad=SPM_QUAD_ORDER4, stream=None):
+        eps = np.ascontiguousarray(eps, dtype=np.complex128)
+        grad = None if grad_eps is None else np.ascontiguousarray(grad_eps, dtype=np.complex128)
+        if eps.size != n ** 3 or (grad is not None and grad.size != 3 * n ** 3):
+            raise ValueError("eps must have n^3 and grad_eps 3 n^3 entries")
+        h = ctypes.c_void_p()
+        _check(lib.spm_create_problem(n, float(omega), _ptr(eps), _ptr(grad), quad, _stream(stream),
+                                      ctypes.byref(h)))
+        self.h = h
+        self.n = n
+        self.omega = float(omega)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.spm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        n, k, u = ctypes.c_int(), ctypes.c_double(), ctypes.c_longlong()
+        _check(lib.spm_problem_info(self.h, ctypes.byref(n), ctypes.byref(k), ctypes.byref(u)))
+        return n.value, k.value, u.value
+
+    # ---- operator
+    def apply_A(self, x, y, stream=None):
+        _check(lib.spm_apply_A(self.h, _prec_of(x), _ptr(x), _ptr(y), _nrhs(x, self.n), _stream(stream)))
+        return y
+
+    def apply_QA(self, x, y, stream=None):
+        _check(lib.spm_apply_QA(self.h, _prec_of(x), _ptr(x), _ptr(y), _nrhs(x, self.n), _stream(stream)))
+        return y
+
+    def apply_Q(self, v, y, stream=None):
+        _check(lib.spm_apply_Q(self.h, _prec_of(v), _ptr(v), _ptr(y), _nrhs(v, self.n), _stream(stream)))
+        return y
+
+    # ---- stencils and S
+    def build_stencils(self, factor_prec=SPM_C128):
+        _check(lib.spm_build_stencils(self.h, factor_prec))
+
+    def set_stencils(self, alpha, beta):
+        a = np.ascontiguousarray(alpha, dtype=np.complex128)
+        b = np.ascontiguousarray(beta, dtype=np.complex128)
+        if a.size != 27 * 81 * 3 or b.size != 27 * 108 * 3:
+            raise ValueError("alpha must be [27][81][3] and beta [27][108][3]")
+        _check(lib.spm_set_stencils(self.h, _ptr(a), _ptr(b)))
+
+    def get_stencils(self):
+        a = np.zeros((27, 81, 3), np.complex128)
+        b = np.zeros((27, 108, 3), np.complex128)
+        sv = np.zeros((27, 81), np.float64)
+        _check(lib.spm_get_stencils(self.h, _ptr(a), _ptr(b), _ptr(sv)))
+        return a, b, sv
+
+    def factor_S(self, prec=SPM_C128):
+        _check(lib.spm_factor_S(self.h, prec))
+
+    def apply_S(self, x, y, stream=None):
+        _check(lib.spm_apply_S(self.h, _prec_of(x), _ptr(x), _ptr(y), _nrhs(x, self.n), _stream(stream)))
+        return y
+
+    def solve_S(self, b, x, stream=None):
+        _check(lib.spm_solve_S(self.h, _prec_of(b), _ptr(b), _ptr(x), _nrhs(b, self.n), _stream(stream)))
+        return x
+
+    # ---- solving
+    def incident_plane_wave(self, directions, polarisations, e, stream=None):
+        d = np.ascontiguousarray(directions, dtype=np.float64).reshape(-1, 3)
+        p = np.ascontiguousarray(polarisations, dtype=np.float64).reshape(-1, 3)
+        _check(lib.spm_incident_plane_wave(self.h, _prec_of(e), _ptr(d), _ptr(p), d.shape[0], _ptr(e),
+                                           _stream(stream)))
+        return e
+
+    def rhs_from_incident(self, einc, g, stream=None):
+        _check(lib.spm_rhs_from_incident(self.h, _ptr(einc), _ptr(g), _nrhs(einc, self.n), _stream(stream)))
+        return g
+
+    def solve(self, g, x, prec=SPM_MIXED, tol=1e-6, maxit=500, restart=20, check=True):
+        info = SolveInfo()
+        st = lib.spm_solve(self.h, prec, _ptr(g), _ptr(x), _nrhs(g, self.n), float(tol), int(maxit), int(restart),
+                           ctypes.byref(info))
+        if check:
+            _check(st)
+        return info, st
+
+    def kernel_entries(self):
+        W = 2 * self.n - 1
+        out = np.zeros((4, W, W, W), np.complex128)
+        _check(lib.spm_kernel_entries(self.h, _ptr(out)))
+        return out

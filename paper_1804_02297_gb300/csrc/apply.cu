@@ -1,0 +1,508 @@
+// Matrix-free apply of the Nystrom operator A = I + [k^2 G, G^d][m; p]
+// (Eq. discrete_block) by zero-padded FFT convolution, plus the sparsifying
+// row combination Q (Eq. nbr_i_block_alpha).
+//
+// Five passes per chunk of right-hand sides, each a batch of 1-D FFTs along
+// one axis done in shared memory (fft.cuh):
+//   xfwd : w = [m E^1, m E^2, m E^3, p.E] formed on the fly, FFT along x
+//          (n inputs zero-padded to L = 2n)          -> W1[b][4][z<n][y<n][xi<L]
+//   yfwd : FFT along y (n -> L)                      -> W2[b][4][z<n][eta<L][xi<L]
+//   zprod: FFT along z (n -> L), Fourier-side product
+//          yhat_d = K0 what_d + K_d what_4  (K0 = k^2 Ghat/L^3, K_d = Ghat^d/L^3),
+//          inverse FFT along z, keep z < n           -> W2 fields 0..2 (in place)
+//   yinv : inverse FFT along eta, keep y < n         -> V1[b][3][z][y][xi] (in W1)
+//   xinv : inverse FFT along xi, keep x < n, y = x + result
+// The kernel spectra are stored as one octant [4][n+1]^3: Ghat is even in each
+// frequency, Ghat^d is odd in frequency d and even in the others.
+#include "fft.cuh"
+
+namespace {
+
+constexpr int NT = 256; // threads per block for every FFT pass
+
+template <typename R> struct tile_cfg;
+template <> struct tile_cfg<float> { static constexpr int TXMAX = 16; };
+template <> struct tile_cfg<double> { static constexpr int TXMAX = 8; };
+
+// -------------------------------------------------------------- xfwd
+// One block handles `nl` grid rows (b, z, y); four lines (w_1..w_4) per row.
+template <typename R>
+__global__ void __launch_bounds__(NT) k_xfwd(const typename cplx_of<R>::type *__restrict__ x,
+                                             const typename cplx_of<R>::type *__restrict__ m,
+                                             const typename cplx_of<R>::type *__restrict__ p,
+                                             typename cplx_of<R>::type *__restrict__ W1, int n, int L,
+                                             int logL, int nrows, int nl,
+                                             const typename cplx_of<R>::type *__restrict__ tw)
+{
+    using C = typename cplx_of<R>::type;
+    extern __shared__ unsigned char smem_raw[];
+    C *buf0 = reinterpret_cast<C *>(smem_raw);
+    C *buf1 = buf0 + 4 * nl * L;
+    const long n2 = (long)n * n, n3 = n2 * n;
+    const int row0 = blockIdx.x * nl;
+    for (int idx = threadIdx.x; idx < nl * L; idx += blockDim.x) {
+        int r = idx / L, xx = idx - r * L;
+        int g = row0 + r;
+        C w0 = czero<C>(), w1 = czero<C>(), w2 = czero<C>(), w3 = czero<C>();
+        if (xx < n && g < nrows) {
+            long b = g / n2, zy = g - b * n2;
+            long off = zy * n + xx;
+            const C *xb = x + b * 3 * n3;
+            C e0 = xb[off], e1 = xb[n3 + off], e2 = xb[2 * n3 + off];
+            C mm = m[off];
+            w0 = cmul(mm, e0);
+            w1 = cmul(mm, e1);
+            w2 = cmul(mm, e2);
+            w3 = cfma(p[off], e0, cfma(p[n3 + off], e1, cmul(p[2 * n3 + off], e2)));
+        }
+        buf0[(0 * nl + r) * L + xx] = w0;
+        buf0[(1 * nl + r) * L + xx] = w1;
+        buf0[(2 * nl + r) * L + xx] = w2;
+        buf0[(3 * nl + r) * L + xx] = w3;
+    }
+    __syncthreads();
+    C *res = smem_fft<-1>(buf0, buf1, L, logL, 4 * nl, L, tw);
+    for (int idx = threadIdx.x; idx < 4 * nl * L; idx += blockDim.x) {
+        int line = idx / L, xi = idx - line * L;
+        int f = line / nl, r = line - f * nl;
+        int g = row0 + r;
+        if (g < nrows) {
+            long b = g / n2, zy = g - b * n2;
+            W1[((b * 4 + f) * n2 + zy) * L + xi] = res[idx];
+        }
+    }
+}
+
+// -------------------------------------------------------------- strided lines
+// Lines along a strided axis.  Element (b, f, z, pos, i) of the input sits at
+//   in[b*ib + f*if_ + z*iz + pos*inner + i], 0 <= pos < nin, 0 <= i < inner,
+// and is written to out[b*ob + f*of + z*oz + pos*inner + i], 0 <= pos < nout.
+// grid = (inner/TX, nz, nb*F); each block transforms TX adjacent lines.
+template <typename R, int DIR>
+__global__ void __launch_bounds__(NT) k_cols(const typename cplx_of<R>::type *in,
+                                             typename cplx_of<R>::type *out, int L, int logL,
+                                             int nin, int nout, long inner, int F, long ib,
+                                             long if_, long iz, long ob, long of, long oz, int TX,
+                                             const typename cplx_of<R>::type *__restrict__ tw)
+{
+    using C = typename cplx_of<R>::type;
+    extern __shared__ unsigned char smem_raw[];
+    const int ls = L + 1;
+    C *buf0 = reinterpret_cast<C *>(smem_raw);
+    C *buf1 = buf0 + TX * ls;
+    const long i0 = (long)blockIdx.x * TX;
+    const int z = blockIdx.y;
+    const int b = blockIdx.z / F, f = blockIdx.z - (blockIdx.z / F) * F;
+    const C *src = in + b * ib + f * if_ + z * iz + i0;
+    C *dst = out + b * ob + f * of + z * oz + i0;
+    for (int idx = threadIdx.x; idx < TX * L; idx += blockDim.x) {
+        int pos = idx / TX, t = idx - pos * TX;
+        buf0[t * ls + pos] = pos < nin ? src[pos * inner + t] : czero<C>();
+    }
+    __syncthreads();
+    C *res = smem_fft<DIR>(buf0, buf1, L, logL, TX, ls, tw);
+    for (int idx = threadIdx.x; idx < TX * nout; idx += blockDim.x) {
+        int pos = idx / TX, t = idx - pos * TX;
+        dst[pos * inner + t] = res[t * ls + pos];
+    }
+}
+
+// -------------------------------------------------------------- zprod
+// Lines along z of W2[b][4][z<n][eta][xi]; TX adjacent (eta, xi) columns per block.
+template <typename R>
+__global__ void __launch_bounds__(NT) k_zprod(typename cplx_of<R>::type *W2,
+                                              const typename cplx_of<R>::type *__restrict__ spec,
+                                              int n, int L, int logL, int TX,
+                                              const typename cplx_of<R>::type *__restrict__ tw)
+{
+    using C = typename cplx_of<R>::type;
+    extern __shared__ unsigned char smem_raw[];
+    const int ls = L + 1;
+    C *w4 = reinterpret_cast<C *>(smem_raw);
+    C *buf0 = w4 + TX * ls;
+    C *buf1 = buf0 + TX * ls;
+    const long L2 = (long)L * L;
+    const long i0 = (long)blockIdx.x * TX;
+    const int b = blockIdx.y;
+    const long fstride = (long)n * L2;
+    C *base = W2 + (long)b * 4 * fstride + i0;
+    const int n1 = n + 1;
+    const long oct = (long)n1 * n1 * n1;
+
+    // what_4 first; it stays in shared memory for the three components
+    for (int idx = threadIdx.x; idx < TX * L; idx += blockDim.x) {
+        int pos = idx / TX, t = idx - pos * TX;
+        buf0[t * ls + pos] = pos < n ? base[3 * fstride + pos * L2 + t] : czero<C>();
+    }
+    __syncthreads();
+    C *res = smem_fft<-1>(buf0, buf1, L, logL, TX, ls, tw);
+    for (int idx = threadIdx.x; idx < TX * ls; idx += blockDim.x) w4[idx] = res[idx];
+    __syncthreads();
+
+    for (int d = 0; d < 3; ++d) {
+        for (int idx = threadIdx.x; idx < TX * L; idx += blockDim.x) {
+            int pos = idx / TX, t = idx - pos * TX;
+            buf0[t * ls + pos] = pos < n ? base[d * fstride + pos * L2 + t] : czero<C>();
+        }
+        __syncthreads();
+        C *wd = smem_fft<-1>(buf0, buf1, L, logL, TX, ls, tw);
+        C *other = (wd == buf0) ? buf1 : buf0;
+        for (int idx = threadIdx.x; idx < TX * L; idx += blockDim.x) {
+            int t = idx / L, zeta = idx - t * L;
+            long col = i0 + t;
+            int eta = (int)(col / L), xi = (int)(col - (long)eta * L);
+            int a1 = xi <= n ? xi : L - xi;
+            int a2 = eta <= n ? eta : L - eta;
+            int a3 = zeta <= n ? zeta : L - zeta;
+            long o = ((long)a3 * n1 + a2) * n1 + a1;
+            C K0 = spec[o];
+            C Kd = spec[(1 + d) * oct + o];
+            int fr = d == 0 ? xi : (d == 1 ? eta : zeta);
+            if (fr > n) { Kd.x = -Kd.x; Kd.y = -Kd.y; }
+            other[t * ls + zeta] = cfma(K0, wd[t * ls + zeta], cmul(Kd, w4[t * ls + zeta]));
+        }
+        __syncthreads();
+        C *yd = smem_fft<1>(other, wd, L, logL, TX, ls, tw);
+        for (int idx = threadIdx.x; idx < TX * n; idx += blockDim.x) {
+            int pos = idx / TX, t = idx - pos * TX;
+            base[d * fstride + pos * L2 + t] = yd[t * ls + pos];
+        }
+        __syncthreads();
+    }
+}
+
+// -------------------------------------------------------------- xinv
+// Rows r of V1[b][3][z][y][xi] (length L) -> y[r*n + x] = x_in[r*n + x] + IFFT(row)[x], x < n.
+template <typename R>
+__global__ void __launch_bounds__(NT) k_xinv(const typename cplx_of<R>::type *__restrict__ V1,
+                                             const typename cplx_of<R>::type *__restrict__ xin,
+                                             typename cplx_of<R>::type *__restrict__ y, int n, int L,
+                                             int logL, long nrows, int nl,
+                                             const typename cplx_of<R>::type *__restrict__ tw)
+{
+    using C = typename cplx_of<R>::type;
+    extern __shared__ unsigned char smem_raw[];
+    C *buf0 = reinterpret_cast<C *>(smem_raw);
+    C *buf1 = buf0 + nl * L;
+    const long row0 = (long)blockIdx.x * nl;
+    for (int idx = threadIdx.x; idx < nl * L; idx += blockDim.x) {
+        int r = idx / L;
+        long g = row0 + r;
+        buf0[idx] = g < nrows ? V1[row0 * L + idx] : czero<C>();
+    }
+    __syncthreads();
+    C *res = smem_fft<1>(buf0, buf1, L, logL, nl, L, tw);
+    for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
+        int r = idx / n, xx = idx - r * n;
+        long g = row0 + r;
+        if (g < nrows) y[g * n + xx] = xin[g * n + xx] + res[r * L + xx];
+    }
+}
+
+// -------------------------------------------------------------- Q gather
+// (Q v)_{i,c} = sum_{(d,o) in tau(class i)} alpha[class][(d,o)][c] v^d_{i+o}.
+// alpha packed [27][81][3]; row (d,o) = d*T + o, offsets enumerated o3, o2, o1.
+template <typename R>
+__global__ void k_qgather(const typename cplx_of<R>::type *__restrict__ v,
+                          const typename cplx_of<R>::type *__restrict__ alpha,
+                          typename cplx_of<R>::type *__restrict__ y, int n, long total)
+{
+    using C = typename cplx_of<R>::type;
+    long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= total) return;
+    const long n3 = (long)n * n * n;
+    long b = gid / n3, i = gid - b * n3;
+    int i1 = (int)(i % n), i2 = (int)((i / n) % n), i3 = (int)(i / ((long)n * n));
+    int c1 = i1 == 0 ? 0 : (i1 == n - 1 ? 2 : 1);
+    int c2 = i2 == 0 ? 0 : (i2 == n - 1 ? 2 : 1);
+    int c3 = i3 == 0 ? 0 : (i3 == n - 1 ? 2 : 1);
+    int cls = c1 + 3 * c2 + 9 * c3;
+    int lo1 = c1 == 0 ? 0 : -1, hi1 = c1 == 2 ? 0 : 1;
+    int lo2 = c2 == 0 ? 0 : -1, hi2 = c2 == 2 ? 0 : 1;
+    int lo3 = c3 == 0 ? 0 : -1, hi3 = c3 == 2 ? 0 : 1;
+    int T = (hi1 - lo1 + 1) * (hi2 - lo2 + 1) * (hi3 - lo3 + 1);
+    const C *al = alpha + (long)cls * 81 * 3;
+    const C *vb = v + b * 3 * n3;
+    C acc0 = czero<C>(), acc1 = czero<C>(), acc2 = czero<C>();
+    int o = 0;
+    for (int o3 = lo3; o3 <= hi3; ++o3)
+        for (int o2 = lo2; o2 <= hi2; ++o2)
+            for (int o1 = lo1; o1 <= hi1; ++o1, ++o) {
+                long j = ((long)(i3 + o3) * n + (i2 + o2)) * n + (i1 + o1);
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    C val = vb[d * n3 + j];
+                    const C *ar = al + (d * T + o) * 3;
+                    acc0 = cfma(ar[0], val, acc0);
+                    acc1 = cfma(ar[1], val, acc1);
+                    acc2 = cfma(ar[2], val, acc2);
+                }
+            }
+    C *yb = y + b * 3 * n3;
+    yb[i] = acc0;
+    yb[n3 + i] = acc1;
+    yb[2 * n3 + i] = acc2;
+}
+
+template <typename R>
+spm_status apply_A_typed(spm_problem_s *P, const void *xv, void *yv, int nrhs, cudaStream_t s)
+{
+    using C = typename cplx_of<R>::type;
+    const int n = P->n, L = P->L, logL = P->logL;
+    const long n2 = (long)n * n, n3 = n2 * n, L2 = (long)L * L;
+    const C *x = reinterpret_cast<const C *>(xv);
+    C *y = reinterpret_cast<C *>(yv);
+    const bool dbl = sizeof(R) == 8;
+    const C *m = dbl ? P->m128.as<C>() : P->m64.as<C>();
+    const C *p = dbl ? P->p128.as<C>() : P->p64.as<C>();
+    const C *spec = dbl ? P->spec128.as<C>() : P->spec64.as<C>();
+    const C *tw = dbl ? P->tw128.as<C>() : P->tw64.as<C>();
+    const int chunk = dbl ? P->chunk128 : P->chunk64;
+    const long w1 = 4 * n2 * L, w2 = 4 * (long)n * L2; // per RHS, complex elements
+    SPM_TRY(P->work.ensure(sizeof(C) * (size_t)chunk * (w1 + w2)));
+    C *W1 = P->work.as<C>();
+    C *W2 = W1 + (long)chunk * w1;
+
+    int TX = tile_cfg<R>::TXMAX;
+    while (TX > 2 && 3 * TX * (L + 1) * (int)sizeof(C) > 100 * 1024) TX >>= 1;
+    if (TX > L) TX = L; // a tile never spans more than one line width
+    const int nlx = L >= 256 ? 1 : 256 / L;
+
+    for (int b0 = 0; b0 < nrhs; b0 += chunk) {
+        const int nb = nrhs - b0 < chunk ? nrhs - b0 : chunk;
+        const C *xb = x + (long)b0 * 3 * n3;
+        C *yb = y + (long)b0 * 3 * n3;
+        {   // xfwd
+            long rows = (long)nb * n2;
+            int grid = (int)((rows + nlx - 1) / nlx);
+            size_t sm = 2 * sizeof(C) * 4 * nlx * L;
+            k_xfwd<R><<<grid, NT, sm, s>>>(xb, m, p, W1, n, L, logL, (int)rows, nlx, tw);
+        }
+        {   // yfwd: W1[b][f][z][y<n][xi] -> W2[b][f][z][eta][xi]
+            dim3 grid((unsigned)(L / TX), (unsigned)n, (unsigned)(nb * 4));
+            size_t sm = 2 * sizeof(C) * TX * (L + 1);
+            k_cols<R, -1><<<grid, NT, sm, s>>>(W1, W2, L, logL, n, L, L, 4, 4 * n2 * L, n2 * L, n * (long)L,
+                                                4 * (long)n * L2, (long)n * L2, L2, TX, tw);
+        }
+        {   // zprod
+            dim3 grid((unsigned)(L2 / TX), (unsigned)nb);
+            size_t sm = 3 * sizeof(C) * TX * (L + 1);
+            k_zprod<R><<<grid, NT, sm, s>>>(W2, spec, n, L, logL, TX, tw);
+        }
+        {   // yinv: W2 fields 0..2 -> V1[b][3][z][y<n][xi] in W1
+            dim3 grid((unsigned)(L / TX), (unsigned)n, (unsigned)(nb * 3));
+            size_t sm = 2 * sizeof(C) * TX * (L + 1);
+            k_cols<R, 1><<<grid, NT, sm, s>>>(W2, W1, L, logL, L, n, L, 3, 4 * (long)n * L2, (long)n * L2, L2,
+                                               3 * n2 * L, n2 * L, n * (long)L, TX, tw);
+        }
+        {   // xinv
+            long rows = (long)nb * 3 * n2;
+            int grid = (int)((rows + nlx - 1) / nlx);
+            size_t sm = 2 * sizeof(C) * nlx * L;
+            k_xinv<R><<<grid, NT, sm, s>>>(W1, xb, yb, n, L, logL, rows, nlx, tw);
+        }
+    }
+    SPM_CUDA_TRY(cudaGetLastError());
+    return SPM_OK;
+}
+
+template <typename R>
+spm_status apply_Q_typed(spm_problem_s *P, const void *vv, void *yv, int nrhs, cudaStream_t s)
+{
+    using C = typename cplx_of<R>::type;
+    const int n = P->n;
+    const long total = (long)nrhs * n * n * n;
+    const C *alpha = sizeof(R) == 8 ? P->alpha128.as<C>() : P->alpha64.as<C>();
+    int grid = (int)((total + 255) / 256);
+    k_qgather<R><<<grid, 256, 0, s>>>(reinterpret_cast<const C *>(vv), alpha, reinterpret_cast<C *>(yv), n, total);
+    SPM_CUDA_TRY(cudaGetLastError());
+    return SPM_OK;
+}
+
+} // namespace
+
+spm_status spm_apply_A_impl(spm_problem_s *P, int prec, const void *x, void *y, int nrhs, cudaStream_t s)
+{
+    return prec == SPM_C128 ? apply_A_typed<double>(P, x, y, nrhs, s) : apply_A_typed<float>(P, x, y, nrhs, s);
+}
+
+spm_status spm_apply_Q_impl(spm_problem_s *P, int prec, const void *v, void *y, int nrhs, cudaStream_t s)
+{
+    return prec == SPM_C128 ? apply_Q_typed<double>(P, v, y, nrhs, s) : apply_Q_typed<float>(P, v, y, nrhs, s);
+}
+
+// ------------------------------------------------------------------ spectra
+namespace {
+
+// Circulant embedding of one kernel on the L^3 grid: slot v in [0,L) holds the
+// entry for offset t = v (v < n) or v - L (v > n); slot n is zero.
+// Entries (Section 2): G_t = h^3 G(t h), G^d_t = h^3 dG/dx_d(t h) off the
+// diagonal; ORDER4 corrections at t = 0 (G) and t = +-e_d (G^d).
+__device__ void kernel_entry_dev(int t1, int t2, int t3, double h, double k, int quad, double Z, double2 out[4])
+{
+    const double inv4pi = 0.079577471545947667884; // 1/(4 pi)
+    if (t1 == 0 && t2 == 0 && t3 == 0) {
+        double zc = quad == 0 ? Z : 0.0;
+        out[0] = make_double2(-h * h * zc * inv4pi, h * h * h * k * inv4pi);
+        out[1] = out[2] = out[3] = make_double2(0.0, 0.0);
+        return;
+    }
+    double x1 = t1 * h, x2 = t2 * h, x3 = t3 * h;
+    double r = sqrt(x1 * x1 + x2 * x2 + x3 * x3);
+    double sn, cs;
+    sincos(k * r, &sn, &cs);
+    double h3 = h * h * h;
+    double g = h3 * inv4pi / r;
+    out[0] = make_double2(g * cs, g * sn);
+    // (i k r - 1) e^{ikr} = (-cs - k r sn) + i (k r cs - sn)
+    double re = -cs - k * r * sn, im = k * r * cs - sn;
+    double f = h3 * inv4pi / (r * r * r);
+    double xs[3] = {x1, x2, x3};
+    int ts[3] = {t1, t2, t3};
+    for (int d = 0; d < 3; ++d) {
+        out[1 + d] = make_double2(f * xs[d] * re, f * xs[d] * im);
+        if (quad == 0) {
+            bool axis = (ts[(d + 1) % 3] == 0) && (ts[(d + 2) % 3] == 0) && (ts[d] == 1 || ts[d] == -1);
+            if (axis) out[1 + d].x += ts[d] * h * Z / (24.0 * 3.14159265358979323846);
+        }
+    }
+}
+
+__global__ void k_fill_circulant(double2 *out, int q, int n, int L, double h, double k, int quad, double Z)
+{
+    long L3 = (long)L * L * L;
+    long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= L3) return;
+    int v1 = (int)(gid % L), v2 = (int)((gid / L) % L), v3 = (int)(gid / ((long)L * L));
+    if (v1 == n || v2 == n || v3 == n) { out[gid] = make_double2(0, 0); return; }
+    int t1 = v1 < n ? v1 : v1 - L, t2 = v2 < n ? v2 : v2 - L, t3 = v3 < n ? v3 : v3 - L;
+    double2 e[4];
+    kernel_entry_dev(t1, t2, t3, h, k, quad, Z, e);
+    out[gid] = e[q];
+}
+
+__global__ void k_entries_table(double2 *out, int n, double h, double k, int quad, double Z)
+{
+    int W = 2 * n - 1;
+    long W3 = (long)W * W * W;
+    long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= W3) return;
+    int a1 = (int)(gid % W), a2 = (int)((gid / W) % W), a3 = (int)(gid / ((long)W * W));
+    double2 e[4];
+    kernel_entry_dev(a1 - (n - 1), a2 - (n - 1), a3 - (n - 1), h, k, quad, Z, e);
+    for (int q = 0; q < 4; ++q) out[q * W3 + gid] = e[q];
+}
+
+__global__ void k_octant(const double2 *__restrict__ full, double2 *spec128, float2 *spec64, int n, int L,
+                         double scale)
+{
+    int n1 = n + 1;
+    long tot = (long)n1 * n1 * n1;
+    long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= tot) return;
+    int a1 = (int)(gid % n1), a2 = (int)((gid / n1) % n1), a3 = (int)(gid / ((long)n1 * n1));
+    double2 v = full[((long)a3 * L + a2) * L + a1];
+    v.x *= scale;
+    v.y *= scale;
+    spec128[gid] = v;
+    spec64[gid] = to_c64(v);
+}
+
+// plain rows: FFT of contiguous rows of length L, in place
+__global__ void __launch_bounds__(NT) k_rows_plain(double2 *a, int L, int logL, long nrows, int nl,
+                                                   const double2 *__restrict__ tw)
+{
+    extern __shared__ unsigned char smem_raw[];
+    double2 *buf0 = reinterpret_cast<double2 *>(smem_raw);
+    double2 *buf1 = buf0 + nl * L;
+    long row0 = (long)blockIdx.x * nl;
+    for (int idx = threadIdx.x; idx < nl * L; idx += blockDim.x) {
+        long g = row0 + idx / L;
+        buf0[idx] = g < nrows ? a[row0 * L + idx] : make_double2(0, 0);
+    }
+    __syncthreads();
+    double2 *res = smem_fft<-1>(buf0, buf1, L, logL, nl, L, tw);
+    for (int idx = threadIdx.x; idx < nl * L; idx += blockDim.x) {
+        long g = row0 + idx / L;
+        if (g < nrows) a[row0 * L + idx] = res[idx];
+    }
+}
+
+} // namespace
+
+spm_status spm_build_spectra(spm_problem_s *P)
+{
+    const int n = P->n, L = P->L, logL = P->logL;
+    const long L3 = (long)L * L * L, L2 = (long)L * L;
+    const int n1 = n + 1;
+    const long oct = (long)n1 * n1 * n1;
+    DevBuf full;
+    SPM_TRY(full.ensure(sizeof(double2) * L3));
+    SPM_TRY(P->spec128.ensure(sizeof(double2) * 4 * oct));
+    SPM_TRY(P->spec64.ensure(sizeof(float2) * 4 * oct));
+    cudaStream_t s = P->stream;
+    double2 *F = full.as<double2>();
+    const double2 *tw = P->tw128.as<double2>();
+    int TX = 8;
+    while (TX > 2 && 2 * TX * (L + 1) * 16 > 100 * 1024) TX >>= 1;
+    if (TX > L) TX = L;
+    const int nlx = L >= 256 ? 1 : 256 / L;
+    for (int q = 0; q < 4; ++q) {
+        k_fill_circulant<<<(unsigned)((L3 + 255) / 256), 256, 0, s>>>(F, q, n, L, P->h, P->k, P->quad, P->zconst);
+        k_rows_plain<<<(unsigned)((L2 + nlx - 1) / nlx), NT, 2 * 16 * nlx * L, s>>>(F, L, logL, L2, nlx, tw);
+        // y: lines along y of [z][y][x]; in place is safe (each block owns its columns)
+        k_cols<double, -1><<<dim3(L / TX, L, 1), NT, 2 * 16 * TX * (L + 1), s>>>(
+            F, F, L, logL, L, L, L, 1, 0, 0, L2, 0, 0, L2, TX, tw);
+        // z: lines along z, inner = L^2
+        k_cols<double, -1><<<dim3((unsigned)(L2 / TX), 1, 1), NT, 2 * 16 * TX * (L + 1), s>>>(
+            F, F, L, logL, L, L, L2, 1, 0, 0, 0, 0, 0, 0, TX, tw);
+        double scale = (q == 0 ? P->k * P->k : 1.0) / (double)L3;
+        k_octant<<<(unsigned)((oct + 255) / 256), 256, 0, s>>>(F, P->spec128.as<double2>() + q * oct,
+                                                               P->spec64.as<float2>() + q * oct, n, L, scale);
+    }
+    SPM_CUDA_TRY(cudaGetLastError());
+    SPM_CUDA_TRY(cudaStreamSynchronize(s));
+    full.release();
+    return SPM_OK;
+}
+
+spm_status spm_entries_device(spm_problem_s *P, DevBuf &t)
+{
+    const int n = P->n, W = 2 * n - 1;
+    const long W3 = (long)W * W * W;
+    SPM_TRY(t.ensure(sizeof(double2) * 4 * W3));
+    k_entries_table<<<(unsigned)((W3 + 255) / 256), 256, 0, P->stream>>>(t.as<double2>(), n, P->h, P->k, P->quad,
+                                                                        P->zconst);
+    SPM_CUDA_TRY(cudaGetLastError());
+    return SPM_OK;
+}
+
+spm_status spm_entries_impl(spm_problem_s *P, double *out_host)
+{
+    const int n = P->n, W = 2 * n - 1;
+    const long W3 = (long)W * W * W;
+    DevBuf t;
+    SPM_TRY(spm_entries_device(P, t));
+    SPM_CUDA_TRY(cudaMemcpyAsync(out_host, t.ptr, sizeof(double2) * 4 * W3, cudaMemcpyDeviceToHost, P->stream));
+    SPM_CUDA_TRY(cudaStreamSynchronize(P->stream));
+    t.release();
+    return SPM_OK;
+}
+
+// The largest smem request of the FFT passes exceeds the 48 KB default; opt in once.
+spm_status spm_apply_init_attributes()
+{
+    const int big = 200 * 1024;
+    SPM_CUDA_TRY(cudaFuncSetAttribute(k_xfwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    SPM_CUDA_TRY(cudaFuncSetAttribute(k_xfwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    SPM_CUDA_TRY(cudaFuncSetAttribute(k_cols<float, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    SPM_CUDA_TRY(cudaFuncSetAttribute(k_cols<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    SPM_CUDA_TRY(cudaFuncSetAttribute(k_cols<double, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    SPM_CUDA_TRY(cudaFuncSetAttribute(k_cols<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    SPM_CUDA_TRY(cudaFuncSetAttribute(k_zprod<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    SPM_CUDA_TRY(cudaFuncSetAttribute(k_zprod<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    SPM_CUDA_TRY(cudaFuncSetAttribute(k_xinv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    SPM_CUDA_TRY(cudaFuncSetAttribute(k_xinv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    SPM_CUDA_TRY(cudaFuncSetAttribute(k_rows_plain, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    return SPM_OK;
+}

@@ -1,0 +1,155 @@
+// Shared device/host helpers of libspm: complex arithmetic on float2/double2,
+// error plumbing and the problem handle.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/spm.h"
+
+// ------------------------------------------------------------ complex types
+template <typename R> struct cplx_of;
+template <> struct cplx_of<float> { using type = float2; };
+template <> struct cplx_of<double> { using type = double2; };
+
+__host__ __device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 operator-(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+
+template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b)
+{
+    C r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+// a * conj(b)
+template <typename C> __host__ __device__ __forceinline__ C cmulc(C a, C b)
+{
+    C r;
+    r.x = a.x * b.x + a.y * b.y;
+    r.y = a.y * b.x - a.x * b.y;
+    return r;
+}
+// c + a * b
+template <typename C> __host__ __device__ __forceinline__ C cfma(C a, C b, C c)
+{
+    C r;
+    r.x = c.x + a.x * b.x - a.y * b.y;
+    r.y = c.y + a.x * b.y + a.y * b.x;
+    return r;
+}
+template <typename C> __host__ __device__ __forceinline__ C cscale(C a, decltype(a.x) s)
+{
+    C r;
+    r.x = a.x * s;
+    r.y = a.y * s;
+    return r;
+}
+template <typename C> __host__ __device__ __forceinline__ C czero()
+{
+    C r;
+    r.x = 0;
+    r.y = 0;
+    return r;
+}
+// multiply by -i (forward) or +i (inverse): DIR = -1 -> -i, +1 -> +i
+template <int DIR, typename C> __host__ __device__ __forceinline__ C mul_i(C a)
+{
+    C r;
+    if (DIR < 0) { r.x = a.y; r.y = -a.x; }
+    else { r.x = -a.y; r.y = a.x; }
+    return r;
+}
+template <typename C> __host__ __device__ __forceinline__ C conj_of(C a)
+{
+    C r;
+    r.x = a.x;
+    r.y = -a.y;
+    return r;
+}
+__host__ __device__ __forceinline__ float2 to_c64(double2 a) { return make_float2((float)a.x, (float)a.y); }
+
+// ------------------------------------------------------------ errors
+void spm_set_error(const char *fmt, ...);
+
+#define SPM_CUDA_TRY(expr)                                                                    \
+    do {                                                                                      \
+        cudaError_t _e = (expr);                                                              \
+        if (_e != cudaSuccess) {                                                              \
+            spm_set_error("%s failed at %s:%d: %s", #expr, __FILE__, __LINE__,                \
+                          cudaGetErrorString(_e));                                            \
+            return _e == cudaErrorMemoryAllocation ? SPM_ERR_OOM : SPM_ERR_CUDA;              \
+        }                                                                                     \
+    } while (0)
+
+#define SPM_TRY(expr)                                                                         \
+    do {                                                                                      \
+        spm_status _s = (expr);                                                               \
+        if (_s != SPM_OK) return _s;                                                          \
+    } while (0)
+
+static inline int ilog2(int v)
+{
+    int r = 0;
+    while ((1 << r) < v) ++r;
+    return r;
+}
+
+// ------------------------------------------------------------ device buffer
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    spm_status ensure(size_t want);
+    void release();
+    template <typename T> T *as() const { return reinterpret_cast<T *>(ptr); }
+};
+
+// ------------------------------------------------------------ sparse factor
+struct NDFactor; // nested-dissection multifrontal factor (sparse.cu)
+
+// ------------------------------------------------------------ the handle
+struct spm_problem_s {
+    int n = 0, L = 0, logL = 0;
+    double k = 0, h = 0;
+    int quad = 0;
+    double zconst = 0;
+    cudaStream_t stream = nullptr;
+
+    // medium on the grid: m (n^3), p (3 n^3)
+    DevBuf m128, p128, m64, p64;
+    // kernel spectra, octant [4][n+1]^3 with k^2/L^3 and 1/L^3 folded in
+    DevBuf spec128, spec64;
+    // twiddles exp(-2 pi i j / L), j < L
+    DevBuf tw128, tw64;
+    // apply workspace
+    DevBuf work;
+    int chunk128 = 1, chunk64 = 1; // right-hand sides per pass chunk
+
+    // stencils
+    bool have_stencils = false;
+    std::vector<double> alpha_h, beta_h, sv_h; // packed host copies (complex interleaved)
+    DevBuf alpha128, alpha64, beta128;
+    // assembled S (block CSR with 3x3 complex blocks, 27-point pattern)
+    bool have_S = false;
+    DevBuf S128, S64; // [n^3][27][3][3] complex; absent neighbours hold zeros
+    NDFactor *fac128 = nullptr, *fac64 = nullptr;
+
+    // solver workspace
+    DevBuf kry;
+};
+
+// ------------------------------------------------------------ internal API
+spm_status spm_apply_A_impl(spm_problem_s *P, int prec, const void *x, void *y, int nrhs, cudaStream_t s);
+spm_status spm_apply_Q_impl(spm_problem_s *P, int prec, const void *v, void *y, int nrhs, cudaStream_t s);
+spm_status spm_build_spectra(spm_problem_s *P);
+spm_status spm_stencils_device(spm_problem_s *P);
+spm_status spm_assemble_S(spm_problem_s *P);
+spm_status spm_apply_S_impl(spm_problem_s *P, int prec, const void *x, void *y, int nrhs, cudaStream_t s);
+spm_status spm_factor_impl(spm_problem_s *P, int prec);
+spm_status spm_solveS_impl(spm_problem_s *P, int prec, const void *b, void *x, int nrhs, cudaStream_t s);
+void spm_factor_free(NDFactor *f);
+spm_status spm_solve_impl(spm_problem_s *P, int prec, const void *g, void *x, int nrhs, double tol,
+                          int maxit, int restart, spm_solve_info *info);

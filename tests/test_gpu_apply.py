@@ -1,0 +1,185 @@
+"""GPU parity of the operator apply (Eq. discrete_block) and Q against the FP64 oracle.
+
+Tolerances: the complex128 path must match the oracle to 1e-12 relative L2 per
+apply.  The complex64 path stores inputs, spectra and intermediates in FP32; its
+error is bounded by a few units of FP32 rounding times log2(L^3) FFT stages
+(about 1e-6 relative), so it is checked at 2e-5 and the value reported.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import spm_inputs as si
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def spm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1804_02297_gb300 as spm
+    return spm
+
+
+def rel(a, b):
+    return np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b))
+
+
+def to_dev(a, dtype=torch.complex128):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda").to(dtype)
+
+
+def make(spm, n, medium="bumps", seed=1, quad=0):
+    k = si.wavenumber_for_grid(n)
+    if medium == "bumps":
+        eps, grad = si.medium_bumps(n, seed=seed, count=8)
+    elif medium == "random":
+        eps, grad = si.random_medium(n, seed)
+    elif medium == "lossy":
+        eps, grad = si.medium_lossy(n, seed, 8, 0.3)
+    else:
+        eps, grad = si.medium_gaussian(n)
+    P = spm.Problem(n, k, eps, grad, quad=quad)
+    m, p = oracle.medium(eps, grad)
+    return P, k, m, p
+
+
+@pytest.mark.parametrize("n", [4, 8, 16])
+@pytest.mark.parametrize("quad", [0, 1])
+def test_kernel_entries_match_oracle(spm, n, quad):
+    P, k, m, p = make(spm, n, quad=quad)
+    got = P.kernel_entries()
+    ref = oracle.kernel_entries(n, k, quad)
+    assert rel(got, ref) < 1e-14
+
+
+@pytest.mark.parametrize("n,medium,nrhs", [(4, "random", 1), (8, "random", 2), (8, "lossy", 1),
+                                           (16, "bumps", 3), (32, "bumps", 1), (32, "random", 2)])
+def test_apply_A_c128_matches_oracle(spm, n, medium, nrhs):
+    P, k, m, p = make(spm, n, medium, seed=n + nrhs)
+    x = si.random_field(n, 100 + n, nrhs)
+    ref = oracle.apply_fft(n, k, m, p, x)
+    y = torch.zeros(x.shape, dtype=torch.complex128, device="cuda")
+    P.apply_A(to_dev(x), y)
+    torch.cuda.synchronize()
+    e = rel(y.cpu().numpy(), ref)
+    assert e < 1e-12, e
+    # the scattering part alone, (A - I) x, at the same tolerance relative to itself
+    e2 = rel(y.cpu().numpy() - x, ref - x)
+    assert e2 < 1e-12, e2
+
+
+def test_apply_A_direct_sum_parity(spm):
+    n = 8
+    P, k, m, p = make(spm, n, "random", seed=5)
+    x = si.random_field(n, 7)
+    ref = oracle.apply_direct(n, k, m, p, x)
+    y = torch.zeros(x.shape, dtype=torch.complex128, device="cuda")
+    P.apply_A(to_dev(x), y)
+    torch.cuda.synchronize()
+    assert rel(y.cpu().numpy(), ref) < 1e-12
+
+
+@pytest.mark.parametrize("n,nrhs", [(8, 1), (16, 2), (32, 1), (64, 1)])
+def test_apply_A_c64_error(spm, n, nrhs):
+    P, k, m, p = make(spm, n, "bumps", seed=2)
+    x = si.random_field(n, 200 + n, nrhs)
+    ref = oracle.apply_fft(n, k, m, p, x)
+    y = torch.zeros(x.shape, dtype=torch.complex64, device="cuda")
+    P.apply_A(to_dev(x, torch.complex64), y)
+    torch.cuda.synchronize()
+    got = y.cpu().numpy().astype(np.complex128)
+    e = rel(got - x, ref - x)  # error of the scattering part, relative to itself
+    print(f"c64 n={n}: rel err of (A-I)x = {e:.2e}, of Ax = {rel(got, ref):.2e}")
+    assert e < 2e-5, e
+
+
+def test_apply_A_full_size_n64_c128(spm):
+    """Full-size workload grid (n = 64, 8 seeded bumps): the whole field against the oracle."""
+    n = 64
+    P, k, m, p = make(spm, n, "bumps", seed=2)
+    x = si.random_field(n, 64)
+    ref = oracle.apply_fft(n, k, m, p, x)
+    y = torch.zeros(x.shape, dtype=torch.complex128, device="cuda")
+    P.apply_A(to_dev(x), y)
+    torch.cuda.synchronize()
+    assert rel(y.cpu().numpy(), ref) < 1e-12
+
+
+def test_vacuum_is_identity(spm):
+    n = 8
+    eps = np.ones((n, n, n), np.complex128)
+    grad = np.zeros((3, n, n, n), np.complex128)
+    P = spm.Problem(n, 3.0, eps, grad)
+    x = si.random_field(n, 3, 2)
+    y = torch.zeros(x.shape, dtype=torch.complex128, device="cuda")
+    P.apply_A(to_dev(x), y)
+    torch.cuda.synchronize()
+    assert np.array_equal(y.cpu().numpy(), x)
+
+
+def test_zero_rhs_and_bad_args(spm):
+    n = 8
+    P, k, m, p = make(spm, n)
+    x = torch.zeros((0, 3, n, n, n), dtype=torch.complex128, device="cuda")
+    P.apply_A(x, x.clone())
+    with pytest.raises(spm.SpmError):
+        y = torch.zeros((3, n, n, n), dtype=torch.complex128, device="cuda")
+        P.apply_A(y, y)
+    with pytest.raises(spm.SpmError):
+        P.apply_QA(torch.zeros((3, n, n, n), dtype=torch.complex128, device="cuda"),
+                   torch.zeros((3, n, n, n), dtype=torch.complex128, device="cuda"))
+
+
+@pytest.mark.parametrize("n", [4, 8])
+def test_apply_Q_and_QA_with_oracle_stencils(spm, n):
+    P, k, m, p = make(spm, n, "random", seed=9)
+    al, be, _ = oracle.all_stencils(n, k)
+    P.set_stencils(al, be)
+    v = si.random_field(n, 31, 2)
+    ref_q = oracle.apply_Q(n, al, v)
+    y = torch.zeros(v.shape, dtype=torch.complex128, device="cuda")
+    P.apply_Q(to_dev(v), y)
+    torch.cuda.synchronize()
+    assert rel(y.cpu().numpy(), ref_q) < 1e-14
+    ref_qa = oracle.apply_Q(n, al, oracle.apply_fft(n, k, m, p, v))
+    P.apply_QA(to_dev(v), y)
+    torch.cuda.synchronize()
+    assert rel(y.cpu().numpy(), ref_qa) < 1e-12
+    y64 = torch.zeros(v.shape, dtype=torch.complex64, device="cuda")
+    P.apply_QA(to_dev(v, torch.complex64), y64)
+    torch.cuda.synchronize()
+    assert rel(y64.cpu().numpy().astype(np.complex128), ref_qa) < 2e-5
+
+
+def test_apply_S_matches_oracle_dense_S(spm):
+    n = 5 if False else 8
+    P, k, m, p = make(spm, n, "random", seed=4)
+    al, be, _ = oracle.all_stencils(n, k)
+    P.set_stencils(al, be)
+    S = oracle.dense_S(n, m, p, al, be)
+    x = si.random_field(n, 8)
+    ref = (S @ x.ravel()).reshape(x.shape)
+    y = torch.zeros(x.shape, dtype=torch.complex128, device="cuda")
+    P.apply_S(to_dev(x), y)
+    torch.cuda.synchronize()
+    assert rel(y.cpu().numpy(), ref) < 1e-14
+
+
+def test_plane_wave_and_rhs(spm):
+    n = 16
+    P, k, m, p = make(spm, n, "gaussian")
+    e = torch.zeros((2, 3, n, n, n), dtype=torch.complex128, device="cuda")
+    dirs = [(0, 0, 1), (1, 0, 0)]
+    pols = [(1, 0, 0), (0, 0, 1)]
+    P.incident_plane_wave(dirs, pols, e)
+    ref = np.stack([si.plane_wave(n, k, d, q) for d, q in zip(dirs, pols)])
+    assert rel(e.cpu().numpy(), ref) < 1e-14
+    g = torch.zeros_like(e)
+    P.rhs_from_incident(e, g)
+    torch.cuda.synchronize()
+    gref = ref - oracle.apply_fft(n, k, m, p, ref)
+    assert rel(g.cpu().numpy(), gref) < 1e-12
