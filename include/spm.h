@@ -144,8 +144,8 @@ spm_status spm_solve_S(spm_problem prob, spm_prec prec, const void *b_dev, void 
 /* ------------------------------------------------------------- solving */
 
 typedef struct {
-    int iterations;         /* preconditioned GMRES iterations, summed over RHS and restarts */
-    int outer_steps;        /* FP64 outer refinement steps (SPM_MIXED), else restarts */
+    int iterations;         /* preconditioned GMRES iterations of the batch (all RHS advance together) */
+    int outer_steps;        /* FP64 outer steps: one GMRES(restart) cycle each */
     double true_relres;     /* max over RHS of ||g - A x|| / ||g|| in FP64 at exit */
     double solve_ms;        /* wall time of the call */
 } spm_solve_info;

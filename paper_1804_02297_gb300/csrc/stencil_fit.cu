@@ -254,9 +254,18 @@ __global__ void __launch_bounds__(256) k_gram_eig(const double2 *__restrict__ E,
     }
     __syncthreads();
 
+    // largest diagonal entry: rounding level of the whole matrix
+    __shared__ double dmax;
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int i = 0; i < C; ++i) m = fmax(m, fabs(H[i * C + i].x));
+        dmax = m;
+    }
+    __syncthreads();
+    const double floor_abs = 4e-17 * dmax;
     const int NP = (C + 1) & ~1; // players, one dummy if C is odd
     const int npairs = NP / 2;
-    for (int sweep = 0; sweep < 30; ++sweep) {
+    for (int sweep = 0; sweep < 40; ++sweep) {
         if (threadIdx.x == 0) off_bits = 0ull;
         __syncthreads();
         for (int round = 0; round < NP - 1; ++round) {
@@ -276,8 +285,8 @@ __global__ void __launch_bounds__(256) k_gram_eig(const double2 *__restrict__ E,
                 double2 b = H[p * C + q];
                 double ab = hypot(b.x, b.y);
                 double scale = sqrt(fabs(a * c));
-                if (ab == 0.0 || ab <= 1e-17 * scale) continue;
-                double rel = scale > 0 ? ab / scale : 1.0;
+                if (ab == 0.0 || ab <= 1e-16 * scale || ab <= floor_abs) continue;
+                double rel = ab / fmax(scale, floor_abs);
                 atomicMax(&off_bits, (unsigned long long)__double_as_longlong(rel)); // positive doubles order as integers
                 double zeta = (c - a) / (2.0 * ab);
                 double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
@@ -299,7 +308,7 @@ __global__ void __launch_bounds__(256) k_gram_eig(const double2 *__restrict__ E,
                 H[q * C + col] = make_double2(sn * hp.x + cs * hq.x, sn * hp.y + cs * hq.y);
             }
             __syncthreads();
-            // columns: H <- H J, V <- V J
+            // columns: H <- H J, V <- V J; the rotated pair is zeroed exactly
             for (int idx = threadIdx.x; idx < npairs * C; idx += blockDim.x) {
                 int k = idx / C, row = idx % C;
                 int p = rp[k], q = rq[k];
@@ -307,8 +316,13 @@ __global__ void __launch_bounds__(256) k_gram_eig(const double2 *__restrict__ E,
                 double cs = rc[k], sn = rs[k];
                 double2 em = rph[k]; // e^{-i phi}
                 double2 hp = H[row * C + p], hq = cmul(em, H[row * C + q]);
-                H[row * C + p] = make_double2(cs * hp.x - sn * hq.x, cs * hp.y - sn * hq.y);
-                H[row * C + q] = make_double2(sn * hp.x + cs * hq.x, sn * hp.y + cs * hq.y);
+                double2 np_ = make_double2(cs * hp.x - sn * hq.x, cs * hp.y - sn * hq.y);
+                double2 nq_ = make_double2(sn * hp.x + cs * hq.x, sn * hp.y + cs * hq.y);
+                if (row == p) nq_ = make_double2(0.0, 0.0);
+                if (row == q) np_ = make_double2(0.0, 0.0);
+                if (row == p || row == q) { (row == p ? np_ : nq_).y = 0.0; }
+                H[row * C + p] = np_;
+                H[row * C + q] = nq_;
                 double2 vp = V[row * C + p], vq = cmul(em, V[row * C + q]);
                 V[row * C + p] = make_double2(cs * vp.x - sn * vq.x, cs * vp.y - sn * vq.y);
                 V[row * C + q] = make_double2(sn * vp.x + cs * vq.x, sn * vp.y + cs * vq.y);
@@ -316,7 +330,7 @@ __global__ void __launch_bounds__(256) k_gram_eig(const double2 *__restrict__ E,
             __syncthreads();
         }
         __syncthreads();
-        if (__longlong_as_double((long long)off_bits) < 1e-15) break;
+        if (__longlong_as_double((long long)off_bits) < 1e-14) break;
         __syncthreads();
     }
     // sort eigenvalues ascending (selection on one thread; C <= 81)
@@ -334,7 +348,7 @@ __global__ void __launch_bounds__(256) k_gram_eig(const double2 *__restrict__ E,
         }
         for (int c = 0; c < 3; ++c)
             for (int r = 0; r < C; ++r) alpha_out[r * 3 + c] = conj_of(V[r * C + idx[c]]);
-        if (__longlong_as_double((long long)off_bits) >= 1e-12) atomicExch(status, 1);
+        if (__longlong_as_double((long long)off_bits) >= 1e-10) atomicExch(status, 1);
     }
 }
 
