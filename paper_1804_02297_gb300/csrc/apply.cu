@@ -15,6 +15,7 @@
 // The kernel spectra are stored as one octant [4][n+1]^3: Ghat is even in each
 // frequency, Ghat^d is odd in frequency d and even in the others.
 #include "fft.cuh"
+#include "fft_reg.cuh"
 
 namespace {
 
@@ -23,55 +24,6 @@ constexpr int NT = 256; // threads per block for every FFT pass
 template <typename R> struct tile_cfg;
 template <> struct tile_cfg<float> { static constexpr int TXMAX = 16; };
 template <> struct tile_cfg<double> { static constexpr int TXMAX = 8; };
-
-// -------------------------------------------------------------- xfwd
-// One block handles `nl` grid rows (b, z, y); four lines (w_1..w_4) per row.
-template <typename R>
-__global__ void __launch_bounds__(NT) k_xfwd(const typename cplx_of<R>::type *__restrict__ x,
-                                             const typename cplx_of<R>::type *__restrict__ m,
-                                             const typename cplx_of<R>::type *__restrict__ p,
-                                             typename cplx_of<R>::type *__restrict__ W1, int n, int L,
-                                             int logL, int nrows, int nl,
-                                             const typename cplx_of<R>::type *__restrict__ tw)
-{
-    using C = typename cplx_of<R>::type;
-    extern __shared__ unsigned char smem_raw[];
-    C *buf0 = reinterpret_cast<C *>(smem_raw);
-    C *buf1 = buf0 + 4 * nl * L;
-    const long n2 = (long)n * n, n3 = n2 * n;
-    const int row0 = blockIdx.x * nl;
-    for (int idx = threadIdx.x; idx < nl * L; idx += blockDim.x) {
-        int r = idx / L, xx = idx - r * L;
-        int g = row0 + r;
-        C w0 = czero<C>(), w1 = czero<C>(), w2 = czero<C>(), w3 = czero<C>();
-        if (xx < n && g < nrows) {
-            long b = g / n2, zy = g - b * n2;
-            long off = zy * n + xx;
-            const C *xb = x + b * 3 * n3;
-            C e0 = xb[off], e1 = xb[n3 + off], e2 = xb[2 * n3 + off];
-            C mm = m[off];
-            w0 = cmul(mm, e0);
-            w1 = cmul(mm, e1);
-            w2 = cmul(mm, e2);
-            w3 = cfma(p[off], e0, cfma(p[n3 + off], e1, cmul(p[2 * n3 + off], e2)));
-        }
-        buf0[(0 * nl + r) * L + xx] = w0;
-        buf0[(1 * nl + r) * L + xx] = w1;
-        buf0[(2 * nl + r) * L + xx] = w2;
-        buf0[(3 * nl + r) * L + xx] = w3;
-    }
-    __syncthreads();
-    C *res = smem_fft<-1>(buf0, buf1, L, logL, 4 * nl, L, tw);
-    for (int idx = threadIdx.x; idx < 4 * nl * L; idx += blockDim.x) {
-        int line = idx / L, xi = idx - line * L;
-        int f = line / nl, r = line - f * nl;
-        int g = row0 + r;
-        if (g < nrows) {
-            long b = g / n2, zy = g - b * n2;
-            W1[((b * 4 + f) * n2 + zy) * L + xi] = res[idx];
-        }
-    }
-}
 
 // -------------------------------------------------------------- strided lines
 // Lines along a strided axis.  Element (b, f, z, pos, i) of the input sits at
@@ -104,98 +56,6 @@ __global__ void __launch_bounds__(NT) k_cols(const typename cplx_of<R>::type *in
     for (int idx = threadIdx.x; idx < TX * nout; idx += blockDim.x) {
         int pos = idx / TX, t = idx - pos * TX;
         dst[pos * inner + t] = res[t * ls + pos];
-    }
-}
-
-// -------------------------------------------------------------- zprod
-// Lines along z of W2[b][4][z<n][eta][xi]; TX adjacent (eta, xi) columns per block.
-template <typename R>
-__global__ void __launch_bounds__(NT) k_zprod(typename cplx_of<R>::type *W2,
-                                              const typename cplx_of<R>::type *__restrict__ spec,
-                                              int n, int L, int logL, int TX,
-                                              const typename cplx_of<R>::type *__restrict__ tw)
-{
-    using C = typename cplx_of<R>::type;
-    extern __shared__ unsigned char smem_raw[];
-    const int ls = L + 1;
-    C *w4 = reinterpret_cast<C *>(smem_raw);
-    C *buf0 = w4 + TX * ls;
-    C *buf1 = buf0 + TX * ls;
-    const long L2 = (long)L * L;
-    const long i0 = (long)blockIdx.x * TX;
-    const int b = blockIdx.y;
-    const long fstride = (long)n * L2;
-    C *base = W2 + (long)b * 4 * fstride + i0;
-    const int n1 = n + 1;
-    const long oct = (long)n1 * n1 * n1;
-
-    // what_4 first; it stays in shared memory for the three components
-    for (int idx = threadIdx.x; idx < TX * L; idx += blockDim.x) {
-        int pos = idx / TX, t = idx - pos * TX;
-        buf0[t * ls + pos] = pos < n ? base[3 * fstride + pos * L2 + t] : czero<C>();
-    }
-    __syncthreads();
-    C *res = smem_fft<-1>(buf0, buf1, L, logL, TX, ls, tw);
-    for (int idx = threadIdx.x; idx < TX * ls; idx += blockDim.x) w4[idx] = res[idx];
-    __syncthreads();
-
-    for (int d = 0; d < 3; ++d) {
-        for (int idx = threadIdx.x; idx < TX * L; idx += blockDim.x) {
-            int pos = idx / TX, t = idx - pos * TX;
-            buf0[t * ls + pos] = pos < n ? base[d * fstride + pos * L2 + t] : czero<C>();
-        }
-        __syncthreads();
-        C *wd = smem_fft<-1>(buf0, buf1, L, logL, TX, ls, tw);
-        C *other = (wd == buf0) ? buf1 : buf0;
-        for (int idx = threadIdx.x; idx < TX * L; idx += blockDim.x) {
-            int t = idx / L, zeta = idx - t * L;
-            long col = i0 + t;
-            int eta = (int)(col / L), xi = (int)(col - (long)eta * L);
-            int a1 = xi <= n ? xi : L - xi;
-            int a2 = eta <= n ? eta : L - eta;
-            int a3 = zeta <= n ? zeta : L - zeta;
-            long o = ((long)a3 * n1 + a2) * n1 + a1;
-            C K0 = spec[o];
-            C Kd = spec[(1 + d) * oct + o];
-            int fr = d == 0 ? xi : (d == 1 ? eta : zeta);
-            if (fr > n) { Kd.x = -Kd.x; Kd.y = -Kd.y; }
-            other[t * ls + zeta] = cfma(K0, wd[t * ls + zeta], cmul(Kd, w4[t * ls + zeta]));
-        }
-        __syncthreads();
-        C *yd = smem_fft<1>(other, wd, L, logL, TX, ls, tw);
-        for (int idx = threadIdx.x; idx < TX * n; idx += blockDim.x) {
-            int pos = idx / TX, t = idx - pos * TX;
-            base[d * fstride + pos * L2 + t] = yd[t * ls + pos];
-        }
-        __syncthreads();
-    }
-}
-
-// -------------------------------------------------------------- xinv
-// Rows r of V1[b][3][z][y][xi] (length L) -> y[r*n + x] = x_in[r*n + x] + IFFT(row)[x], x < n.
-template <typename R>
-__global__ void __launch_bounds__(NT) k_xinv(const typename cplx_of<R>::type *__restrict__ V1,
-                                             const typename cplx_of<R>::type *__restrict__ xin,
-                                             typename cplx_of<R>::type *__restrict__ y, int n, int L,
-                                             int logL, long nrows, int nl,
-                                             const typename cplx_of<R>::type *__restrict__ tw)
-{
-    using C = typename cplx_of<R>::type;
-    extern __shared__ unsigned char smem_raw[];
-    C *buf0 = reinterpret_cast<C *>(smem_raw);
-    C *buf1 = buf0 + nl * L;
-    const long row0 = (long)blockIdx.x * nl;
-    for (int idx = threadIdx.x; idx < nl * L; idx += blockDim.x) {
-        int r = idx / L;
-        long g = row0 + r;
-        buf0[idx] = g < nrows ? V1[row0 * L + idx] : czero<C>();
-    }
-    __syncthreads();
-    C *res = smem_fft<1>(buf0, buf1, L, logL, nl, L, tw);
-    for (int idx = threadIdx.x; idx < nl * n; idx += blockDim.x) {
-        int r = idx / n, xx = idx - r * n;
-        long g = row0 + r;
-        if (g < nrows) y[g * n + xx] = xin[g * n + xx] + res[r * L + xx];
     }
 }
 
@@ -244,11 +104,230 @@ __global__ void k_qgather(const typename cplx_of<R>::type *__restrict__ v,
     yb[2 * n3 + i] = acc2;
 }
 
+// ================================================================ v2 passes
+// Register-resident line FFTs (fft_reg.cuh): thread t of a line holds elements
+// t + T m, m = 0..7, T = L/8.  Strided passes use TX adjacent columns per block
+// with thread (c, t) at tid = c + TX t, so each load/store instruction of a warp
+// touches whole 128-byte rows.
+
+// columns per strided-pass block: 128-byte rows, fewer at L = 512 so the block
+// (TX * L/8 threads) keeps at least 128 registers per thread
+template <typename R, int L> struct tx_of {
+    static constexpr int w = (sizeof(R) == 4 ? 16 : 8) / (L >= 512 ? 2 : 1);
+    static constexpr int v = w < L ? w : L; // never wider than a row of L elements
+};
+
+template <int L> __device__ __forceinline__ int xpad(int pos) { return pos + (pos >> 3); }
+
+// xfwd: w_f of one grid row per line, FFT along x (pruned), 4 fields in turn.
+template <typename R, int L>
+__global__ void __launch_bounds__(256) k2_xfwd(const typename cplx_of<R>::type *__restrict__ x,
+                                               const typename cplx_of<R>::type *__restrict__ m,
+                                               const typename cplx_of<R>::type *__restrict__ p,
+                                               typename cplx_of<R>::type *__restrict__ W1, int nrows,
+                                               const typename cplx_of<R>::type *__restrict__ tw)
+{
+    using C = typename cplx_of<R>::type;
+    constexpr int T = L / 8, n = L / 2, LPB = 256 / T > 0 ? 256 / T : 1, LS = L + L / 8;
+    extern __shared__ unsigned char smem_raw[];
+    C *sm = reinterpret_cast<C *>(smem_raw);
+    const int line = threadIdx.x / T, t = threadIdx.x % T;
+    const int g = blockIdx.x * LPB + line;
+    const bool ok = g < nrows;
+    const long n2 = (long)n * n, n3 = n2 * n;
+    const long b = ok ? g / n2 : 0, zy = ok ? g - b * n2 : 0;
+    C e[3][4], mm[4], pp[3][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        long off = zy * n + t + T * q;
+        if (ok) {
+            const C *xb = x + b * 3 * n3;
+            e[0][q] = xb[off]; e[1][q] = xb[n3 + off]; e[2][q] = xb[2 * n3 + off];
+            mm[q] = m[off];
+            pp[0][q] = p[off]; pp[1][q] = p[n3 + off]; pp[2][q] = p[2 * n3 + off];
+        } else {
+            e[0][q] = e[1][q] = e[2][q] = mm[q] = pp[0][q] = pp[1][q] = pp[2][q] = czero<C>();
+        }
+    }
+    C *lb = sm + line * LS;
+    auto buf = [&](int pos) -> C & { return lb[xpad<L>(pos)]; };
+    auto sync = [&]() { if (T <= 32) __syncwarp(); else __syncthreads(); };
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        C v[8];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (f < 3) v[q] = cmul(mm[q], e[f][q]);
+            else v[q] = cfma(pp[0][q], e[0][q], cfma(pp[1][q], e[1][q], cmul(pp[2][q], e[2][q])));
+            v[q + 4] = czero<C>();
+        }
+        fftr::fft_line<-1, L, true>(v, t, buf, sync, tw);
+        if (ok) {
+            C *dst = W1 + ((b * 4 + f) * n2 + zy) * L;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) dst[t + T * q] = v[q];
+        }
+        sync();
+    }
+}
+
+// Strided lines: element (b, f, z, pos, i) at in[b*ib + f*if_ + z*iz + pos*inner + i];
+// grid (inner/TX, nz, nb*F).  nin, nout in {L/2, L}.
+template <typename R, int L, int DIR, bool PRUNE>
+__global__ void __launch_bounds__(tx_of<R, L>::v * L / 8) k2_cols(const typename cplx_of<R>::type *in, typename cplx_of<R>::type *out,
+                                                int nout, long inner, int F, long ib, long if_, long iz, long ob,
+                                                long of, long oz, const typename cplx_of<R>::type *__restrict__ tw)
+{
+    using C = typename cplx_of<R>::type;
+    constexpr int T = L / 8, TX = tx_of<R, L>::v;
+    extern __shared__ unsigned char smem_raw[];
+    C *sm = reinterpret_cast<C *>(smem_raw);
+    const int c = threadIdx.x % TX, t = threadIdx.x / TX;
+    const long i0 = (long)blockIdx.x * TX;
+    const int z = blockIdx.y;
+    const int b = blockIdx.z / F, f = blockIdx.z % F;
+    const C *src = in + b * ib + f * if_ + z * iz + i0 + c;
+    C *dst = out + b * ob + f * of + z * oz + i0 + c;
+    C v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = (!PRUNE || q < 4) ? src[(long)(t + T * q) * inner] : czero<C>();
+    auto buf = [&](int pos) -> C & { return sm[pos * TX + c]; };
+    auto sync = [&]() { __syncthreads(); };
+    fftr::fft_line<DIR, L, PRUNE>(v, t, buf, sync, tw);
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+        if (t + T * q < nout) dst[(long)(t + T * q) * inner] = v[q];
+}
+
+// zprod: lines along z of W2[b][4][z<n][eta][xi] (TX adjacent columns), product
+// with the octant spectra, inverse along z, keep z < n (in place, fields 0..2).
+template <typename R, int L>
+__global__ void __launch_bounds__(tx_of<R, L>::v * L / 8) k2_zprod(typename cplx_of<R>::type *W2,
+                                                 const typename cplx_of<R>::type *__restrict__ spec,
+                                                 const typename cplx_of<R>::type *__restrict__ tw)
+{
+    using C = typename cplx_of<R>::type;
+    constexpr int T = L / 8, TX = tx_of<R, L>::v, n = L / 2, n1 = n + 1;
+    constexpr long L2 = (long)L * L, oct = (long)n1 * n1 * n1, fs = (long)n * L * L;
+    extern __shared__ unsigned char smem_raw[];
+    C *sm = reinterpret_cast<C *>(smem_raw);
+    const int c = threadIdx.x % TX, t = threadIdx.x / TX;
+    const long col = (long)blockIdx.x * TX + c;
+    const int b = blockIdx.y;
+    C *base = W2 + (long)b * 4 * fs + col;
+    const int eta = (int)(col / L), xi = (int)(col % L);
+    const int a1 = xi <= n ? xi : L - xi, a2 = eta <= n ? eta : L - eta;
+    auto buf = [&](int pos) -> C & { return sm[pos * TX + c]; };
+    auto sync = [&]() { __syncthreads(); };
+    C w4[8];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) w4[q] = base[3 * fs + (long)(t + T * q) * L2];
+#pragma unroll
+    for (int q = 4; q < 8; ++q) w4[q] = czero<C>();
+    fftr::fft_line<-1, L, true>(w4, t, buf, sync, tw);
+#pragma unroll 1
+    for (int d = 0; d < 3; ++d) {
+        C v[8];
+        sync();
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = base[d * fs + (long)(t + T * q) * L2];
+#pragma unroll
+        for (int q = 4; q < 8; ++q) v[q] = czero<C>();
+        fftr::fft_line<-1, L, true>(v, t, buf, sync, tw);
+        const int fr_fixed = d == 0 ? xi : eta;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int zeta = t + T * q;
+            const int a3 = zeta <= n ? zeta : L - zeta;
+            const long o = ((long)a3 * n1 + a2) * n1 + a1;
+            C K0 = spec[o], Kd = spec[(1 + d) * oct + o];
+            const int fr = d == 2 ? zeta : fr_fixed;
+            if (fr > n) { Kd.x = -Kd.x; Kd.y = -Kd.y; }
+            v[q] = cfma(K0, v[q], cmul(Kd, w4[q]));
+        }
+        sync();
+        fftr::fft_line<1, L, false>(v, t, buf, sync, tw);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) base[d * fs + (long)(t + T * q) * L2] = v[q];
+    }
+}
+
+// xinv: rows of V1 (length L) -> y = x + IFFT(row)[x < n]
+template <typename R, int L>
+__global__ void __launch_bounds__(256) k2_xinv(const typename cplx_of<R>::type *__restrict__ V1,
+                                               const typename cplx_of<R>::type *__restrict__ xin,
+                                               typename cplx_of<R>::type *__restrict__ y, long nrows,
+                                               const typename cplx_of<R>::type *__restrict__ tw)
+{
+    using C = typename cplx_of<R>::type;
+    constexpr int T = L / 8, n = L / 2, LPB = 256 / T > 0 ? 256 / T : 1, LS = L + L / 8;
+    extern __shared__ unsigned char smem_raw[];
+    C *sm = reinterpret_cast<C *>(smem_raw);
+    const int line = threadIdx.x / T, t = threadIdx.x % T;
+    const long g = (long)blockIdx.x * LPB + line;
+    const bool ok = g < nrows;
+    C v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = ok ? V1[g * L + t + T * q] : czero<C>();
+    C *lb = sm + line * LS;
+    auto buf = [&](int pos) -> C & { return lb[xpad<L>(pos)]; };
+    auto sync = [&]() { if (T <= 32) __syncwarp(); else __syncthreads(); };
+    fftr::fft_line<1, L, false>(v, t, buf, sync, tw);
+    if (ok) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            long o = g * n + t + T * q;
+            y[o] = xin[o] + v[q];
+        }
+    }
+}
+
+template <typename K> void allow_smem(K kernel, size_t bytes)
+{
+    if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename R, int L>
+void apply_chunk_v2(const typename cplx_of<R>::type *xb, typename cplx_of<R>::type *yb,
+                    const typename cplx_of<R>::type *m, const typename cplx_of<R>::type *p,
+                    const typename cplx_of<R>::type *spec, const typename cplx_of<R>::type *tw,
+                    typename cplx_of<R>::type *W1, typename cplx_of<R>::type *W2, int nb, cudaStream_t s)
+{
+    using C = typename cplx_of<R>::type;
+    constexpr int n = L / 2, T = L / 8, TX = tx_of<R, L>::v;
+    constexpr int LPB = 256 / T > 0 ? 256 / T : 1;
+    constexpr size_t sm_rows = sizeof(C) * LPB * (L + L / 8), sm_cols = sizeof(C) * L * TX;
+    static bool attrs = false;
+    if (!attrs) {
+        allow_smem(k2_xfwd<R, L>, sm_rows);
+        allow_smem(k2_xinv<R, L>, sm_rows);
+        allow_smem(k2_cols<R, L, -1, true>, sm_cols);
+        allow_smem(k2_cols<R, L, 1, false>, sm_cols);
+        allow_smem(k2_zprod<R, L>, sm_cols);
+        attrs = true;
+    }
+    const long n2 = (long)n * n, L2 = (long)L * L;
+    const int THR = TX * T; // threads of a strided-pass block
+    {
+        long rows = (long)nb * n2;
+        k2_xfwd<R, L><<<(unsigned)((rows + LPB - 1) / LPB), LPB * T, sm_rows, s>>>(xb, m, p, W1, (int)rows, tw);
+    }
+    k2_cols<R, L, -1, true><<<dim3(L / TX, n, nb * 4), THR, sm_cols, s>>>(
+        W1, W2, L, L, 4, 4 * n2 * L, n2 * L, n * (long)L, 4 * (long)n * L2, (long)n * L2, L2, tw);
+    k2_zprod<R, L><<<dim3((unsigned)(L2 / TX), nb), THR, sm_cols, s>>>(W2, spec, tw);
+    k2_cols<R, L, 1, false><<<dim3(L / TX, n, nb * 3), THR, sm_cols, s>>>(
+        W2, W1, n, L, 3, 4 * (long)n * L2, (long)n * L2, L2, 3 * n2 * L, n2 * L, n * (long)L, tw);
+    {
+        long rows = (long)nb * 3 * n2;
+        k2_xinv<R, L><<<(unsigned)((rows + LPB - 1) / LPB), LPB * T, sm_rows, s>>>(W1, xb, yb, rows, tw);
+    }
+}
+
 template <typename R>
 spm_status apply_A_typed(spm_problem_s *P, const void *xv, void *yv, int nrhs, cudaStream_t s)
 {
     using C = typename cplx_of<R>::type;
-    const int n = P->n, L = P->L, logL = P->logL;
+    const int n = P->n, L = P->L;
     const long n2 = (long)n * n, n3 = n2 * n, L2 = (long)L * L;
     const C *x = reinterpret_cast<const C *>(xv);
     C *y = reinterpret_cast<C *>(yv);
@@ -262,44 +341,19 @@ spm_status apply_A_typed(spm_problem_s *P, const void *xv, void *yv, int nrhs, c
     SPM_TRY(P->work.ensure(sizeof(C) * (size_t)chunk * (w1 + w2)));
     C *W1 = P->work.as<C>();
     C *W2 = W1 + (long)chunk * w1;
-
-    int TX = tile_cfg<R>::TXMAX;
-    while (TX > 2 && 3 * TX * (L + 1) * (int)sizeof(C) > 100 * 1024) TX >>= 1;
-    if (TX > L) TX = L; // a tile never spans more than one line width
-    const int nlx = L >= 256 ? 1 : 256 / L;
-
     for (int b0 = 0; b0 < nrhs; b0 += chunk) {
         const int nb = nrhs - b0 < chunk ? nrhs - b0 : chunk;
         const C *xb = x + (long)b0 * 3 * n3;
         C *yb = y + (long)b0 * 3 * n3;
-        {   // xfwd
-            long rows = (long)nb * n2;
-            int grid = (int)((rows + nlx - 1) / nlx);
-            size_t sm = 2 * sizeof(C) * 4 * nlx * L;
-            k_xfwd<R><<<grid, NT, sm, s>>>(xb, m, p, W1, n, L, logL, (int)rows, nlx, tw);
-        }
-        {   // yfwd: W1[b][f][z][y<n][xi] -> W2[b][f][z][eta][xi]
-            dim3 grid((unsigned)(L / TX), (unsigned)n, (unsigned)(nb * 4));
-            size_t sm = 2 * sizeof(C) * TX * (L + 1);
-            k_cols<R, -1><<<grid, NT, sm, s>>>(W1, W2, L, logL, n, L, L, 4, 4 * n2 * L, n2 * L, n * (long)L,
-                                                4 * (long)n * L2, (long)n * L2, L2, TX, tw);
-        }
-        {   // zprod
-            dim3 grid((unsigned)(L2 / TX), (unsigned)nb);
-            size_t sm = 3 * sizeof(C) * TX * (L + 1);
-            k_zprod<R><<<grid, NT, sm, s>>>(W2, spec, n, L, logL, TX, tw);
-        }
-        {   // yinv: W2 fields 0..2 -> V1[b][3][z][y<n][xi] in W1
-            dim3 grid((unsigned)(L / TX), (unsigned)n, (unsigned)(nb * 3));
-            size_t sm = 2 * sizeof(C) * TX * (L + 1);
-            k_cols<R, 1><<<grid, NT, sm, s>>>(W2, W1, L, logL, L, n, L, 3, 4 * (long)n * L2, (long)n * L2, L2,
-                                               3 * n2 * L, n2 * L, n * (long)L, TX, tw);
-        }
-        {   // xinv
-            long rows = (long)nb * 3 * n2;
-            int grid = (int)((rows + nlx - 1) / nlx);
-            size_t sm = 2 * sizeof(C) * nlx * L;
-            k_xinv<R><<<grid, NT, sm, s>>>(W1, xb, yb, n, L, logL, rows, nlx, tw);
+        switch (L) {
+        case 8: apply_chunk_v2<R, 8>(xb, yb, m, p, spec, tw, W1, W2, nb, s); break;
+        case 16: apply_chunk_v2<R, 16>(xb, yb, m, p, spec, tw, W1, W2, nb, s); break;
+        case 32: apply_chunk_v2<R, 32>(xb, yb, m, p, spec, tw, W1, W2, nb, s); break;
+        case 64: apply_chunk_v2<R, 64>(xb, yb, m, p, spec, tw, W1, W2, nb, s); break;
+        case 128: apply_chunk_v2<R, 128>(xb, yb, m, p, spec, tw, W1, W2, nb, s); break;
+        case 256: apply_chunk_v2<R, 256>(xb, yb, m, p, spec, tw, W1, W2, nb, s); break;
+        case 512: apply_chunk_v2<R, 512>(xb, yb, m, p, spec, tw, W1, W2, nb, s); break;
+        default: spm_set_error("unsupported FFT length %d", L); return SPM_ERR_INVALID_ARG;
         }
     }
     SPM_CUDA_TRY(cudaGetLastError());
@@ -493,16 +547,10 @@ spm_status spm_entries_impl(spm_problem_s *P, double *out_host)
 spm_status spm_apply_init_attributes()
 {
     const int big = 200 * 1024;
-    SPM_CUDA_TRY(cudaFuncSetAttribute(k_xfwd<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    SPM_CUDA_TRY(cudaFuncSetAttribute(k_xfwd<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     SPM_CUDA_TRY(cudaFuncSetAttribute(k_cols<float, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     SPM_CUDA_TRY(cudaFuncSetAttribute(k_cols<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     SPM_CUDA_TRY(cudaFuncSetAttribute(k_cols<double, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     SPM_CUDA_TRY(cudaFuncSetAttribute(k_cols<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    SPM_CUDA_TRY(cudaFuncSetAttribute(k_zprod<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    SPM_CUDA_TRY(cudaFuncSetAttribute(k_zprod<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    SPM_CUDA_TRY(cudaFuncSetAttribute(k_xinv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    SPM_CUDA_TRY(cudaFuncSetAttribute(k_xinv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     SPM_CUDA_TRY(cudaFuncSetAttribute(k_rows_plain, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     return SPM_OK;
 }

@@ -12,10 +12,15 @@
 //   children's Schur complements are extend-added,
 //   F11 = P L U (partial pivoting inside the own block),
 //   X = F11^{-1} F12,   update = F22 - F21 X  -> parent.
-// Solve: forward y_own = F11^{-1} w_own, w_bnd -= F21 y_own (post-order);
-//        backward x_own = y_own - X x_bnd (reverse post-order).
-// Dense blocks use cuSOLVER getrf/getrs and cuBLAS gemm; assembly, extend-add
-// and the gathers/scatters are kernels here.
+// Each node keeps G = [F11^{-1}; F21 F11^{-1}] (front x own) and X = F11^{-1} F12.
+// Solve, one batched pass per tree level:
+//   forward (deepest level first): [y; t] = G w_own, w_own = y, w_bnd -= t
+//   backward (root first):         w_own -= X w_bnd.
+// Nodes of one level have disjoint own unknowns; their boundaries lie on
+// shallower separators, so one launch handles a whole level.  The factor
+// phase uses cuSOLVER getrf/getrs and cuBLAS gemm on the dense fronts;
+// assembly, extend-add, the batched level GEMVs, gathers and scatters are
+// kernels here.
 #include <cublas_v2.h>
 #include <cuComplex.h>
 #include <cusolverDn.h>
@@ -38,6 +43,7 @@ struct Node {
     long rel_off = 0;        // offset of the child-bnd -> parent-front map (unknowns)
     long fac_off = 0;        // persistent factor storage (elements)
     long piv_off = 0;        // pivots
+    int depth = 0;
 };
 
 template <typename R> struct blas_t;
@@ -124,40 +130,6 @@ __global__ void k_copy_block(C *dst, int ldd, const C *__restrict__ src, int lds
     dst[(long)c * ldd + r] = src[(long)c * lds + r];
 }
 
-// gather unknowns of the listed points from the global [b][d][point] vector into a
-// column-major (3*npts x nrhs) block; sign = +1 copy, scatter variants below
-template <typename C>
-__global__ void k_gather(C *dst, const C *__restrict__ w, const int *__restrict__ pts, int npts, long n3, int nrhs)
-{
-    long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    long rows = 3L * npts;
-    if (gid >= rows * nrhs) return;
-    long r = gid % rows, b = gid / rows;
-    int a = (int)(r / 3), c = (int)(r % 3);
-    dst[b * rows + r] = w[(b * 3 + c) * n3 + pts[a]];
-}
-
-template <typename C>
-__global__ void k_scatter(C *w, const C *__restrict__ src, const int *__restrict__ pts, int npts, long n3, int nrhs,
-                          int subtract)
-{
-    long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    long rows = 3L * npts;
-    if (gid >= rows * nrhs) return;
-    long r = gid % rows, b = gid / rows;
-    int a = (int)(r / 3), c = (int)(r % 3);
-    long g = (b * 3 + c) * n3 + pts[a];
-    C s = src[b * rows + r];
-    if (subtract) {
-        C v = w[g];
-        v.x -= s.x;
-        v.y -= s.y;
-        w[g] = v;
-    } else {
-        w[g] = s;
-    }
-}
-
 template <typename C> __global__ void k_zero(C *a, long cnt)
 {
     long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -165,6 +137,141 @@ template <typename C> __global__ void k_zero(C *a, long cnt)
 }
 
 inline unsigned blocks(long cnt, int t = 256) { return (unsigned)((cnt + t - 1) / t); }
+
+// n x n identity in a column-major block with leading dimension ld
+template <typename C> __global__ void k_identity(C *a, int n, int ld)
+{
+    long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (long)n * n) return;
+    int r = (int)(gid % n), c = (int)(gid / n);
+    a[(long)c * ld + r].x = r == c ? 1 : 0;
+    a[(long)c * ld + r].y = 0;
+}
+
+// Level tables.  Per node of a level: its matrix (rows x cols, column-major,
+// ld = rows) at mat_off; packed input block (cols x nrhs) at in_unit * nrhs and
+// output block (rows x nrhs) at out_unit * nrhs, in_unit / out_unit being prefix
+// sums of cols / rows over the level.
+struct LevelNode {
+    long mat_off, in_unit, out_unit;
+    int rows, cols;
+    int own_pts, bnd_pts; // offsets into the point list
+    int nown, nbnd;
+};
+struct Tile {
+    int node, row0, col0;
+};
+constexpr int GT_ROWS = 256, GT_COLS = 256, GT_NB = 4;
+
+// out[node] += M[node][row0:+256, col0:+256] * in[node][col0:+256, :]
+template <typename C>
+__global__ void __launch_bounds__(GT_ROWS) k_level_gemv(const C *__restrict__ M, const LevelNode *__restrict__ nodes,
+                                                        const Tile *__restrict__ tiles, const C *__restrict__ in,
+                                                        C *out, int nrhs)
+{
+    using R = decltype(C{}.x);
+    __shared__ C xs[GT_COLS * GT_NB];
+    const Tile tl = tiles[blockIdx.x];
+    const LevelNode nd = nodes[tl.node];
+    const int r = tl.row0 + threadIdx.x;
+    const int ncol = min(GT_COLS, nd.cols - tl.col0);
+    const C *inb = in + nd.in_unit * nrhs;
+    C *outb = out + nd.out_unit * nrhs;
+    for (int b0 = 0; b0 < nrhs; b0 += GT_NB) {
+        const int nb = min(GT_NB, nrhs - b0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < GT_COLS * GT_NB; i += blockDim.x) {
+            int c = i % GT_COLS, b = i / GT_COLS;
+            C v;
+            v.x = 0;
+            v.y = 0;
+            if (c < ncol && b < nb) v = inb[(long)(b0 + b) * nd.cols + tl.col0 + c];
+            xs[i] = v;
+        }
+        __syncthreads();
+        if (r < nd.rows) {
+            R ax[GT_NB], ay[GT_NB];
+#pragma unroll
+            for (int b = 0; b < GT_NB; ++b) { ax[b] = 0; ay[b] = 0; }
+            const C *col = M + nd.mat_off + (long)tl.col0 * nd.rows + r;
+#pragma unroll 4
+            for (int c = 0; c < ncol; ++c) {
+                C g = col[(long)c * nd.rows];
+#pragma unroll
+                for (int b = 0; b < GT_NB; ++b) {
+                    C xv = xs[b * GT_COLS + c];
+                    ax[b] += g.x * xv.x - g.y * xv.y;
+                    ay[b] += g.x * xv.y + g.y * xv.x;
+                }
+            }
+            for (int b = 0; b < nb; ++b) {
+                C *o = outb + (long)(b0 + b) * nd.rows + r;
+                atomicAdd(&o->x, ax[b]);
+                atomicAdd(&o->y, ay[b]);
+            }
+        }
+    }
+}
+
+// node whose element range [unit[i] * nrhs, unit[i+1] * nrhs) holds gid
+__device__ __forceinline__ int find_node(const long *__restrict__ unit, int nn, long gid, int nrhs)
+{
+    int lo = 0, hi = nn - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) / 2;
+        if (unit[mid] * nrhs <= gid) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// packed input of every node of a level: own (which = 0) or boundary (1) unknowns of w
+template <typename C>
+__global__ void k_level_gather(C *packed, const C *__restrict__ w, const LevelNode *__restrict__ nodes,
+                               const long *__restrict__ in_units, const int *__restrict__ pts, int nn, long n3,
+                               int nrhs, int which)
+{
+    long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= in_units[nn] * nrhs) return;
+    const int id = find_node(in_units, nn, gid, nrhs);
+    const LevelNode nd = nodes[id];
+    long e = gid - in_units[id] * nrhs;
+    long r = e % nd.cols, b = e / nd.cols;
+    int pt = pts[(which ? nd.bnd_pts : nd.own_pts) + (int)(r / 3)];
+    packed[gid] = w[(b * 3 + (r % 3)) * n3 + pt];
+}
+
+// forward (mode 0): w_own = out[0:o3], w_bnd -= out[o3:] (siblings share
+// boundaries: atomic); backward (mode 1): w_own -= out
+template <typename C>
+__global__ void k_level_scatter(C *w, const C *__restrict__ packed, const LevelNode *__restrict__ nodes,
+                                const long *__restrict__ out_units, const int *__restrict__ pts, int nn, long n3,
+                                int nrhs, int mode)
+{
+    long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= out_units[nn] * nrhs) return;
+    const int id = find_node(out_units, nn, gid, nrhs);
+    const LevelNode nd = nodes[id];
+    long e = gid - out_units[id] * nrhs;
+    long r = e % nd.rows, b = e / nd.rows;
+    C v = packed[gid];
+    const int o3 = 3 * nd.nown;
+    if (r < o3) {
+        long g = (b * 3 + (r % 3)) * n3 + pts[nd.own_pts + (int)(r / 3)];
+        if (mode == 0) {
+            w[g] = v;
+        } else {
+            C u = w[g];
+            u.x -= v.x;
+            u.y -= v.y;
+            w[g] = u;
+        }
+    } else {
+        long rb = r - o3;
+        long g = (b * 3 + (rb % 3)) * n3 + pts[nd.bnd_pts + (int)(rb / 3)];
+        atomicAdd(&w[g].x, -v.x);
+        atomicAdd(&w[g].y, -v.y);
+    }
+}
 
 } // namespace
 
@@ -180,6 +287,18 @@ struct NDFactor {
     DevBuf front, stack, work, info; // factor scratch (released after factoring)
     DevBuf solve_ws;
     size_t max_front_unknowns = 0, max_own3 = 0, max_bnd3 = 0;
+    // level tables for the batched solve; levels[0] is the deepest
+    struct Level {
+        int nn_f, nn_b;                // nodes in the forward / backward tables
+        long nodes_f, nodes_b;         // offsets into the LevelNode table
+        long units_f_in, units_f_out, units_b_in, units_b_out; // offsets into the unit table (nn+1 each)
+        long tiles_f, tiles_b;         // offsets into the tile table
+        int ntiles_f, ntiles_b;
+        long pack_f_in, pack_f_out, pack_b_in, pack_b_out; // packed sizes per RHS
+    };
+    std::vector<Level> levels;
+    DevBuf lv_nodes, lv_units, lv_tiles;
+    long max_pack_in = 0, max_pack_out = 0;
     cublasHandle_t cublas = nullptr;
     cusolverDnHandle_t cusolver = nullptr;
     ~NDFactor()
@@ -188,6 +307,7 @@ struct NDFactor {
         if (cusolver) cusolverDnDestroy(cusolver);
         pts.release(); maps.release(); rels.release(); fac.release(); piv.release();
         front.release(); stack.release(); work.release(); info.release(); solve_ws.release();
+        lv_nodes.release(); lv_units.release(); lv_tiles.release();
     }
 };
 
@@ -197,9 +317,10 @@ namespace {
 
 constexpr int LEAF_SIDE = 5;
 
-int build_tree(std::vector<Node> &nodes, const int lo[3], const int hi[3])
+int build_tree(std::vector<Node> &nodes, const int lo[3], const int hi[3], int depth = 0)
 {
     Node nd;
+    nd.depth = depth;
     for (int d = 0; d < 3; ++d) { nd.lo[d] = lo[d]; nd.hi[d] = hi[d]; }
     int axis = 0;
     for (int d = 1; d < 3; ++d) if (hi[d] - lo[d] > hi[axis] - lo[axis]) axis = d;
@@ -210,8 +331,8 @@ int build_tree(std::vector<Node> &nodes, const int lo[3], const int hi[3])
         int lhi[3] = {hi[0], hi[1], hi[2]}, rlo[3] = {lo[0], lo[1], lo[2]};
         lhi[axis] = nd.cut;
         rlo[axis] = nd.cut + 1;
-        nd.left = build_tree(nodes, lo, lhi);
-        nd.right = build_tree(nodes, rlo, hi);
+        nd.left = build_tree(nodes, lo, lhi, depth + 1);
+        nd.right = build_tree(nodes, rlo, hi, depth + 1);
     }
     nodes.push_back(nd);
     return (int)nodes.size() - 1;
@@ -376,11 +497,22 @@ static spm_status factor_typed(spm_problem_s *P, NDFactor *F)
             k_copy_block<C><<<blocks((long)b3 * b3), 256, 0, s>>>(stack + top, b3, front + (long)o3 * f + o3, f, b3, b3);
             top += upd_size[id];
         }
-        // persistent: [F11; F21] (f x o3, ld f) then X (o3 x b3, ld o3)
-        k_copy_block<C><<<blocks((long)f * o3), 256, 0, s>>>(fac + nd.fac_off, f, front, f, f, o3);
-        if (b3 > 0)
-            k_copy_block<C><<<blocks((long)o3 * b3), 256, 0, s>>>(fac + nd.fac_off + (long)f * o3, o3,
-                                                                  front + (long)o3 * f, f, o3, b3);
+        // persistent: G = [F11^{-1}; F21 F11^{-1}] (f x o3, ld f) then X (o3 x b3, ld o3)
+        C *G = fac + nd.fac_off;
+        k_identity<C><<<blocks((long)o3 * o3), 256, 0, s>>>(G, o3, f);
+        if (BT::getrs(F->cusolver, o3, o3, front, f, dpiv + nd.piv_off, G, f, dinfo + 1) != CUSOLVER_STATUS_SUCCESS) {
+            spm_set_error("getrs (inverse) failed at node %d", id);
+            return SPM_ERR_CUDA;
+        }
+        if (b3 > 0) {
+            if (BT::gemm(F->cublas, b3, o3, o3, BT::one(), front + o3, f, G, f, C{0, 0}, G + o3, f) !=
+                CUBLAS_STATUS_SUCCESS) {
+                spm_set_error("gemm (F21 F11^-1) failed at node %d", id);
+                return SPM_ERR_CUDA;
+            }
+            k_copy_block<C><<<blocks((long)o3 * b3), 256, 0, s>>>(G + (long)f * o3, o3, front + (long)o3 * f, f, o3,
+                                                                  b3);
+        }
         SPM_CUDA_TRY(cudaGetLastError());
     }
     int hinfo[2] = {0, 0};
@@ -392,6 +524,70 @@ static spm_status factor_typed(spm_problem_s *P, NDFactor *F)
     if (hinfo[0] != 0 || hinfo[1] != 0) {
         spm_set_error("zero pivot in the multifrontal factor (info %d, %d)", hinfo[0], hinfo[1]);
         return SPM_ERR_NUMERICAL;
+    }
+    // level tables for the batched solve
+    {
+        int maxd = 0;
+        for (const Node &nd : nodes) maxd = std::max(maxd, nd.depth);
+        std::vector<LevelNode> tn;
+        std::vector<long> tu;
+        std::vector<Tile> tt;
+        F->levels.clear();
+        F->max_pack_in = F->max_pack_out = 0;
+        auto add_table = [&](const std::vector<int> &ids, bool fwd, int &nn, long &nodes_off, long &uin, long &uout,
+                             long &tiles_off, int &ntiles, long &pin, long &pout) {
+            nodes_off = (long)tn.size();
+            tiles_off = (long)tt.size();
+            std::vector<long> ui(1, 0), uo(1, 0);
+            nn = 0;
+            for (int id : ids) {
+                const Node &nd = nodes[id];
+                const int o3 = 3 * nd.nown, b3 = 3 * nd.nbnd, f = o3 + b3;
+                LevelNode L;
+                L.rows = fwd ? f : o3;
+                L.cols = fwd ? o3 : b3;
+                if (L.cols == 0) continue;
+                L.mat_off = fwd ? nd.fac_off : nd.fac_off + (long)f * o3;
+                L.in_unit = ui.back();
+                L.out_unit = uo.back();
+                L.own_pts = (int)nd.own_off;
+                L.bnd_pts = (int)nd.bnd_off;
+                L.nown = nd.nown;
+                L.nbnd = nd.nbnd;
+                for (int r0 = 0; r0 < L.rows; r0 += GT_ROWS)
+                    for (int c0 = 0; c0 < L.cols; c0 += GT_COLS) tt.push_back(Tile{nn, r0, c0});
+                tn.push_back(L);
+                ui.push_back(ui.back() + L.cols);
+                uo.push_back(uo.back() + L.rows);
+                ++nn;
+            }
+            uin = (long)tu.size();
+            tu.insert(tu.end(), ui.begin(), ui.end());
+            uout = (long)tu.size();
+            tu.insert(tu.end(), uo.begin(), uo.end());
+            ntiles = (int)(tt.size() - tiles_off);
+            pin = ui.back();
+            pout = uo.back();
+            F->max_pack_in = std::max(F->max_pack_in, pin);
+            F->max_pack_out = std::max(F->max_pack_out, pout);
+        };
+        for (int d = maxd; d >= 0; --d) {
+            std::vector<int> ids;
+            for (int id = 0; id < NN; ++id) if (nodes[id].depth == d) ids.push_back(id);
+            NDFactor::Level lv;
+            add_table(ids, true, lv.nn_f, lv.nodes_f, lv.units_f_in, lv.units_f_out, lv.tiles_f, lv.ntiles_f,
+                      lv.pack_f_in, lv.pack_f_out);
+            add_table(ids, false, lv.nn_b, lv.nodes_b, lv.units_b_in, lv.units_b_out, lv.tiles_b, lv.ntiles_b,
+                      lv.pack_b_in, lv.pack_b_out);
+            F->levels.push_back(lv);
+        }
+        SPM_TRY(F->lv_nodes.ensure(sizeof(LevelNode) * tn.size()));
+        SPM_TRY(F->lv_units.ensure(sizeof(long) * tu.size()));
+        SPM_TRY(F->lv_tiles.ensure(sizeof(Tile) * std::max<size_t>(tt.size(), 1)));
+        SPM_CUDA_TRY(cudaMemcpy(F->lv_nodes.ptr, tn.data(), sizeof(LevelNode) * tn.size(), cudaMemcpyHostToDevice));
+        SPM_CUDA_TRY(cudaMemcpy(F->lv_units.ptr, tu.data(), sizeof(long) * tu.size(), cudaMemcpyHostToDevice));
+        if (!tt.empty())
+            SPM_CUDA_TRY(cudaMemcpy(F->lv_tiles.ptr, tt.data(), sizeof(Tile) * tt.size(), cudaMemcpyHostToDevice));
     }
     (void)n3;
     (void)sizeof(CV);
@@ -407,42 +603,35 @@ static spm_status solve_typed(spm_problem_s *P, NDFactor *F, const void *bv, voi
     const long n3 = (long)n * n * n;
     C *x = reinterpret_cast<C *>(xv);
     SPM_CUDA_TRY(cudaMemcpyAsync(x, bv, sizeof(C) * 3 * n3 * nrhs, cudaMemcpyDeviceToDevice, s));
-    size_t ws = (F->max_own3 + F->max_bnd3) * (size_t)nrhs;
-    SPM_TRY(F->solve_ws.ensure(sizeof(C) * ws));
-    C *y = F->solve_ws.as<C>();
-    C *t = y + F->max_own3 * nrhs;
-    cublasSetStream(F->cublas, s);
-    cusolverDnSetStream(F->cusolver, s);
+    const size_t pin = (size_t)F->max_pack_in * nrhs, pout = (size_t)F->max_pack_out * nrhs;
+    SPM_TRY(F->solve_ws.ensure(sizeof(C) * (pin + pout)));
+    C *in = F->solve_ws.as<C>();
+    C *out = in + pin;
     const int *dpts = F->pts.as<int>();
     const C *fac = F->fac.as<C>();
-    const int *dpiv = F->piv.as<int>();
-    int *dinfo = F->info.ptr ? F->info.as<int>() : nullptr;
-    if (!dinfo) { SPM_TRY(F->info.ensure(sizeof(int) * 2)); dinfo = F->info.as<int>(); }
-    const int NN = (int)F->nodes.size();
-    for (int id = 0; id < NN; ++id) { // forward, post-order
-        const Node &nd = F->nodes[id];
-        const int o3 = 3 * nd.nown, b3 = 3 * nd.nbnd, f = o3 + b3;
-        const C *LU = fac + nd.fac_off;
-        k_gather<C><<<blocks((long)o3 * nrhs), 256, 0, s>>>(y, x, dpts + nd.own_off, nd.nown, n3, nrhs);
-        if (BT::getrs(F->cusolver, o3, nrhs, LU, f, dpiv + nd.piv_off, y, o3, dinfo) != CUSOLVER_STATUS_SUCCESS) {
-            spm_set_error("getrs failed in the forward solve");
-            return SPM_ERR_CUDA;
-        }
-        k_scatter<C><<<blocks((long)o3 * nrhs), 256, 0, s>>>(x, y, dpts + nd.own_off, nd.nown, n3, nrhs, 0);
-        if (b3 > 0) {
-            BT::gemm(F->cublas, b3, nrhs, o3, BT::one(), LU + o3, f, y, o3, C{0, 0}, t, b3);
-            k_scatter<C><<<blocks((long)b3 * nrhs), 256, 0, s>>>(x, t, dpts + nd.bnd_off, nd.nbnd, n3, nrhs, 1);
-        }
+    const LevelNode *tn = F->lv_nodes.as<LevelNode>();
+    const long *tu = F->lv_units.as<long>();
+    const Tile *tt = F->lv_tiles.as<Tile>();
+    const int NL = (int)F->levels.size();
+    for (int l = 0; l < NL; ++l) { // forward, deepest level first
+        const NDFactor::Level &lv = F->levels[l];
+        if (lv.nn_f == 0) continue;
+        k_level_gather<C><<<blocks(lv.pack_f_in * nrhs), 256, 0, s>>>(in, x, tn + lv.nodes_f, tu + lv.units_f_in, dpts,
+                                                                       lv.nn_f, n3, nrhs, 0);
+        SPM_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(C) * lv.pack_f_out * nrhs, s));
+        k_level_gemv<C><<<lv.ntiles_f, GT_ROWS, 0, s>>>(fac, tn + lv.nodes_f, tt + lv.tiles_f, in, out, nrhs);
+        k_level_scatter<C><<<blocks(lv.pack_f_out * nrhs), 256, 0, s>>>(x, out, tn + lv.nodes_f, tu + lv.units_f_out,
+                                                                         dpts, lv.nn_f, n3, nrhs, 0);
     }
-    for (int id = NN - 1; id >= 0; --id) { // backward, reverse post-order
-        const Node &nd = F->nodes[id];
-        const int o3 = 3 * nd.nown, b3 = 3 * nd.nbnd, f = o3 + b3;
-        if (b3 == 0) continue;
-        const C *X = fac + nd.fac_off + (long)f * o3;
-        k_gather<C><<<blocks((long)o3 * nrhs), 256, 0, s>>>(y, x, dpts + nd.own_off, nd.nown, n3, nrhs);
-        k_gather<C><<<blocks((long)b3 * nrhs), 256, 0, s>>>(t, x, dpts + nd.bnd_off, nd.nbnd, n3, nrhs);
-        BT::gemm(F->cublas, o3, nrhs, b3, BT::mone(), X, o3, t, b3, BT::one(), y, o3);
-        k_scatter<C><<<blocks((long)o3 * nrhs), 256, 0, s>>>(x, y, dpts + nd.own_off, nd.nown, n3, nrhs, 0);
+    for (int l = NL - 1; l >= 0; --l) { // backward, root first
+        const NDFactor::Level &lv = F->levels[l];
+        if (lv.nn_b == 0) continue;
+        k_level_gather<C><<<blocks(lv.pack_b_in * nrhs), 256, 0, s>>>(in, x, tn + lv.nodes_b, tu + lv.units_b_in, dpts,
+                                                                       lv.nn_b, n3, nrhs, 1);
+        SPM_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(C) * lv.pack_b_out * nrhs, s));
+        k_level_gemv<C><<<lv.ntiles_b, GT_ROWS, 0, s>>>(fac, tn + lv.nodes_b, tt + lv.tiles_b, in, out, nrhs);
+        k_level_scatter<C><<<blocks(lv.pack_b_out * nrhs), 256, 0, s>>>(x, out, tn + lv.nodes_b, tu + lv.units_b_out,
+                                                                         dpts, lv.nn_b, n3, nrhs, 1);
     }
     SPM_CUDA_TRY(cudaGetLastError());
     return SPM_OK;
