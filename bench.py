@@ -3,8 +3,16 @@
 Default workload (``n64_bumps8``): n = 64 grid (262,144 points, 786,432 complex
 unknowns), k = 16 pi (8 wavelengths at about 8 points per wavelength), eps = 1 +
 tapered sum of 8 seeded Gaussian bumps, one incident plane wave, complex64.
-One step = one application of the operator on the hot path (``--op QA``: Q A,
-the sparsifying row combination after A; ``--op A``: A alone).
+One step = one application of the operator on the hot path: ``--op QA``
+(default) applies A (contrast multiply, zero-padded FFTs, Fourier-side product
+with the four kernel spectra, inverse FFTs, +x) and then the sparsifying row
+combination Q; ``--op A`` applies A alone.
+
+``solve`` (same JSON line): time to a true relative residual of 1e-6 for the
+workload's incident field with the S^-1 Q preconditioned GMRES(20), complex64
+operator and factor inside the FP64 outer loop (``mixed``); ``--solve both``
+adds the plain complex128 solve.  Set-up (stencils, factor) is timed apart from
+the solve, as the paper reports T_setup apart from T_solve.
 
 Timing: W warm-up steps, then K steps, each bracketed by CUDA events on the
 launch stream, with an L2 flush (a 512 MiB buffer write) between steps, barrier
@@ -44,7 +52,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="n64_bumps8")
     ap.add_argument("--prec", default="c64", choices=["c64", "c128"])
-    ap.add_argument("--op", default="A", choices=["A", "QA"])
+    ap.add_argument("--op", default="QA", choices=["A", "QA"])
+    ap.add_argument("--solve", default="mixed", choices=["none", "mixed", "both"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
@@ -133,26 +142,37 @@ class ClockSampler:
 
 
 def cpu_baseline(wl, seconds, op):
-    """FP64 oracle FFT apply on a bounded sample (whole applies until ~seconds)."""
+    """FP64 oracle apply (A, then Q for op QA) on a bounded sample: whole applies
+    until about `seconds` have passed.  For Q the stencil tables are seeded
+    random numbers: the oracle's cost does not depend on their values."""
     import oracle
     n, k = wl["n"], wl["omega"]
     m, p = oracle.medium(wl["eps"], wl["grad"])
     x = wl["einc"][0]
     F = oracle.FFTOperator(n, k)
-    F.apply(m, p, x)  # warm
+    alpha = si.random_field(1, 99, 27 * 81).reshape(-1)[: 27 * 81 * 3].reshape(27, 81, 3)
+
+    def one():
+        y = F.apply(m, p, x)
+        if op == "QA":
+            y = oracle.apply_Q(n, alpha, y)
+        return y
+
+    one()  # warm
     t0 = time.perf_counter()
     count = 0
     while True:
-        F.apply(m, p, x)
+        one()
         count += 1
         if time.perf_counter() - t0 > seconds:
             break
     dt = time.perf_counter() - t0
     F.close()
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    what = "A then Q" if op == "QA" else "A"
     return {"value": count / dt, "unit": "applies/s", "cores": cores, "kind": "oracle",
-            "sample": f"{count} FP64 FFT applies of A (oracle, spectra precomputed) at n={n}; "
-                      f"apply {op} on the GPU side"}
+            "sample": f"{count} FP64 oracle applies of {what} at n={n} (kernel spectra precomputed), "
+                      f"{dt:.1f} s on {cores} host threads"}
 
 
 def run_reference(args):
@@ -165,7 +185,7 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 / cb["value"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-            "config": {"workload": args.workload, "n": wl["n"], "nrhs": 1, "op": "A"},
+            "config": {"workload": args.workload, "n": wl["n"], "nrhs": 1, "op": args.op},
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": "applies/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -190,6 +210,39 @@ def recorded_traffic(workload, prec, op):
     return e.get("dram_bytes_per_apply")
 
 
+def measure_solve(spm, torch, P, wl, args, have_c64_factor):
+    """Time-to-1e-6 of the preconditioned solve (set-up reported separately)."""
+    out = {"tol": 1e-6, "restart": 20}
+    n = wl["n"]
+    t0 = time.perf_counter()
+    if not have_c64_factor:
+        P.build_stencils(spm.SPM_C64)
+    torch.cuda.synchronize()
+    e = torch.from_numpy(wl["einc"][:1]).to("cuda")
+    g = torch.zeros_like(e)
+    P.rhs_from_incident(e, g)
+    modes = [("mixed", spm.SPM_MIXED)]
+    if args.solve == "both":
+        t1 = time.perf_counter()
+        P.factor_S(spm.SPM_C128)
+        out["setup_factor_c128_s"] = time.perf_counter() - t1
+        modes.append(("fp64", spm.SPM_C128))
+    for name, prec in modes:
+        times = []
+        for _ in range(3):
+            x = torch.zeros_like(g)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            info, st = P.solve(g, x, prec=prec, tol=1e-6, maxit=400, restart=20, check=False)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t1)
+        out[name] = {"time_s": float(np.median(times)), "iterations": info.iterations,
+                     "outer_steps": info.outer_steps, "true_relres": info.true_relres, "status": st}
+    if "fp64" in out:
+        out["fp64_over_mixed"] = out["fp64"]["time_s"] / out["mixed"]["time_s"]
+    return out
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -205,8 +258,13 @@ def run_ours(args):
     dtype = torch.complex64 if args.prec == "c64" else torch.complex128
     x = torch.from_numpy(wl["einc"][0]).to(dtype).to("cuda").contiguous()
     y = torch.zeros_like(x)
+    setup = {}
+    if args.op == "QA" or args.solve != "none":
+        t0 = time.perf_counter()
+        P.build_stencils(spm.SPM_C64)  # device stencil fit, S assembly, complex64 factor
+        torch.cuda.synchronize()
+        setup["stencils_assembly_factor_c64_s"] = time.perf_counter() - t0
     if args.op == "QA":
-        P.build_stencils(spm.SPM_C64)
         fn = P.apply_QA
         launches_per_step = 6
     else:
@@ -294,6 +352,9 @@ def run_ours(args):
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
             "step_ms_min": float(np.min(step_ms)), "step_ms_median": float(np.median(step_ms))}
+    if args.solve != "none":
+        line["solve"] = measure_solve(spm, torch, P, wl, args, True)
+        line["solve"]["setup"] = setup
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds, args.op)
     if rank == 0:

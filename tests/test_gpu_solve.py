@@ -141,3 +141,44 @@ def test_solve_error_paths(spm):
     assert st == spm.SPM_ERR_NO_CONVERGENCE
     assert info.iterations >= 2 and np.isfinite(info.true_relres)
     assert np.linalg.norm(x.cpu().numpy()) > 0  # the last iterate is returned
+
+
+def test_solve_full_size_n64_residual_checked_by_oracle(spm):
+    """Full-size workload (n = 64, 8 bumps, plane wave): the oracle recomputes the
+    true residual of the GPU's mixed-precision solution with its own FP64 FFT
+    apply (a full oracle solve at this size is too slow for a test)."""
+    wl = si.workload("n64_bumps8")
+    n, k = wl["n"], wl["omega"]
+    P = spm.Problem(n, k, wl["eps"], wl["grad"])
+    P.build_stencils(spm.SPM_C64)
+    e = dev(wl["einc"])
+    g = torch.zeros_like(e)
+    P.rhs_from_incident(e, g)
+    x = torch.zeros_like(g)
+    info, _ = P.solve(g, x, prec=spm.SPM_MIXED, tol=1e-6, maxit=200)
+    m, p = oracle.medium(wl["eps"], wl["grad"])
+    gh = g.cpu().numpy()[0]
+    xh = x.cpu().numpy()[0]
+    gref = wl["einc"][0] - oracle.apply_fft(n, k, m, p, wl["einc"][0])
+    assert rel(gh, gref) < 1e-12
+    r = gref - oracle.apply_fft(n, k, m, p, xh)
+    relres = np.linalg.norm(r) / np.linalg.norm(gref)
+    print(f"n=64 mixed: iterations {info.iterations}, library relres {info.true_relres:.2e}, oracle relres {relres:.2e}")
+    assert relres <= 1e-6
+    assert abs(relres - info.true_relres) < 1e-3 * max(relres, 1e-12) + 1e-12
+
+
+def test_batched_apply_equals_single(spm):
+    """A block of right-hand sides in one call equals the applies one by one (c64, n = 64)."""
+    n = 64
+    k = si.wavenumber_for_grid(n)
+    eps, grad = si.medium_bumps(n, seed=2, count=8)
+    P = spm.Problem(n, k, eps, grad)
+    X = dev(si.plane_wave_block(n, k, 4), torch.complex64)
+    Y = torch.zeros_like(X)
+    P.apply_A(X, Y)
+    for b in range(4):
+        yb = torch.zeros_like(X[b])
+        P.apply_A(X[b].contiguous(), yb)
+        torch.cuda.synchronize()
+        assert torch.equal(yb, Y[b])
