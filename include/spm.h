@@ -89,6 +89,23 @@ spm_status spm_problem_info(spm_problem prob, int *n, double *k, long long *unkn
 spm_status spm_apply_A(spm_problem prob, spm_prec prec, const void *x_dev, void *y_dev,
                        int nrhs, void *stream);
 
+/* y = A x exactly as spm_apply_A, but the call allocates no device memory.
+ * The paper has no counterpart: this serves callers that cannot allocate when
+ * they apply the operator (device memory owned by another allocator or budget,
+ * or loops that cannot afford cudaMalloc/cudaFree blocking or synchronising the
+ * device).  The pass intermediates live in one fixed 64 MiB device array inside
+ * the library (every GPU that loads the library holds it until the process
+ * exits); right-hand sides are processed one at a time, so the limit is
+ * 24 n^3 complex values: n <= 64 in SPM_C64, n <= 32 in SPM_C128.  Larger
+ * problems return SPM_ERR_INVALID_ARG before any device work.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  All
+ * calls share the array: calls whose work overlaps on the GPU (different
+ * streams, or different handles at once) race on it and give wrong results.
+ * The problem handle itself is created (and allocated) by spm_create_problem. */
+spm_status spm_apply_A_noalloc(spm_problem prob, spm_prec prec, const void *x_dev, void *y_dev,
+                               int nrhs, void *stream);
+
 /* y = Q A x: A as above followed by the sparsifying row combination Q,
  * (Q v)_{i,c} = sum_{(d,o) in tau(class i)} alpha_class[(d,o),c] v^d_{i+o}
  * (Eq. nbr_i_block_alpha; classes of Section 3.2).  Needs stencils

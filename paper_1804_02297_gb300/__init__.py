@@ -25,7 +25,7 @@ EXPORTS = [
     "spm_create_problem", "spm_destroy", "spm_problem_info", "spm_apply_A", "spm_apply_QA", "spm_apply_Q",
     "spm_build_stencils", "spm_set_stencils", "spm_get_stencils", "spm_factor_S", "spm_apply_S",
     "spm_solve_S", "spm_incident_plane_wave", "spm_rhs_from_incident", "spm_solve", "spm_kernel_entries",
-    "spm_lattice_constant", "spm_last_error",
+    "spm_lattice_constant", "spm_last_error", "spm_apply_A_noalloc",
 ]
 
 
@@ -50,6 +50,7 @@ def _load():
         "spm_destroy": [P],
         "spm_problem_info": [P, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)],
         "spm_apply_A": [P, I, P, P, I, P],
+        "spm_apply_A_noalloc": [P, I, P, P, I, P],
         "spm_apply_QA": [P, I, P, P, I, P],
         "spm_apply_Q": [P, I, P, P, I, P],
         "spm_build_stencils": [P, I],
@@ -159,6 +160,11 @@ class Problem:
     # ---- operator
     def apply_A(self, x, y, stream=None):
         _check(lib.spm_apply_A(self.h, _prec_of(x), _ptr(x), _ptr(y), _nrhs(x, self.n), _stream(stream)))
+        return y
+
+    def apply_A_noalloc(self, x, y, stream=None):
+        """y = A x with no device allocation in the call (fixed library scratch)."""
+        _check(lib.spm_apply_A_noalloc(self.h, _prec_of(x), _ptr(x), _ptr(y), _nrhs(x, self.n), _stream(stream)))
         return y
 
     def apply_QA(self, x, y, stream=None):

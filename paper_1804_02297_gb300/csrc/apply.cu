@@ -14,6 +14,8 @@
 //   xinv : inverse FFT along xi, keep x < n, y = x + result
 // The kernel spectra are stored as one octant [4][n+1]^3: Ghat is even in each
 // frequency, Ghat^d is odd in frequency d and even in the others.
+#include <mutex>
+
 #include "fft.cuh"
 #include "fft_reg.cuh"
 
@@ -553,4 +555,104 @@ spm_status spm_apply_init_attributes()
     SPM_CUDA_TRY(cudaFuncSetAttribute(k_cols<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     SPM_CUDA_TRY(cudaFuncSetAttribute(k_rows_plain, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     return SPM_OK;
+}
+
+// ================================================================ no-allocation apply
+// Some callers cannot allocate device memory when they apply the operator: a
+// process whose device memory is owned by another allocator or budget (a pool
+// reserved up front, where a raw cudaMalloc could fail or fragment it), or a
+// latency-bound loop that cannot afford cudaMalloc/cudaFree, which may block
+// or synchronise the device.  spm_apply_A_noalloc serves them: it runs the same
+// passes as spm_apply_A but keeps the pass intermediates (24 n^3 complex values
+// per right-hand side, right-hand sides taken one at a time) in this file-scope
+// device array instead of library-allocated workspace.  Every GPU that loads
+// the library holds the array until the process exits.
+#define SPM_NOALLOC_SCRATCH_BYTES (64ull << 20)
+static __device__ __align__(256) unsigned char g_spm_noalloc_scratch[SPM_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[128] = {}; // device address of the array, per device ordinal
+
+// Host code cannot use the array's name as a device address: look the address
+// up once per device, with that device current.
+spm_status noalloc_scratch(void **out)
+{
+    int dev = 0;
+    SPM_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 128) {
+        spm_set_error("device ordinal %d out of range for the no-allocation scratch table", dev);
+        return SPM_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_spm_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            spm_set_error("cudaGetSymbolAddress of the no-allocation scratch failed: %s", cudaGetErrorString(e));
+            return SPM_ERR_CUDA;
+        }
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return SPM_OK;
+}
+
+template <typename R>
+spm_status apply_A_noalloc_typed(spm_problem_s *P, const void *xv, void *yv, int nrhs, cudaStream_t s)
+{
+    using C = typename cplx_of<R>::type;
+    const int n = P->n, L = P->L;
+    const long n2 = (long)n * n, n3 = n2 * n, L2 = (long)L * L;
+    const long w1 = 4 * n2 * L, w2 = 4 * (long)n * L2;
+    const unsigned long long need = sizeof(C) * (unsigned long long)(w1 + w2);
+    if (need > SPM_NOALLOC_SCRATCH_BYTES) {
+        spm_set_error("spm_apply_A_noalloc: n = %d in %s needs %llu bytes of scratch, above the fixed %llu", n,
+                      sizeof(R) == 8 ? "complex128" : "complex64", need, SPM_NOALLOC_SCRATCH_BYTES);
+        return SPM_ERR_INVALID_ARG;
+    }
+    void *scratch = nullptr;
+    SPM_TRY(noalloc_scratch(&scratch));
+    C *W1 = reinterpret_cast<C *>(scratch);
+    C *W2 = W1 + w1;
+    const bool dbl = sizeof(R) == 8;
+    const C *m = dbl ? P->m128.as<C>() : P->m64.as<C>();
+    const C *p = dbl ? P->p128.as<C>() : P->p64.as<C>();
+    const C *spec = dbl ? P->spec128.as<C>() : P->spec64.as<C>();
+    const C *tw = dbl ? P->tw128.as<C>() : P->tw64.as<C>();
+    const C *x = reinterpret_cast<const C *>(xv);
+    C *y = reinterpret_cast<C *>(yv);
+    // Every pass writes its whole output before the next pass reads it, so no
+    // part of the shared scratch has to be cleared between calls.
+    for (int b = 0; b < nrhs; ++b) {
+        const C *xb = x + (long)b * 3 * n3;
+        C *yb = y + (long)b * 3 * n3;
+        switch (L) {
+        case 8: apply_chunk_v2<R, 8>(xb, yb, m, p, spec, tw, W1, W2, 1, s); break;
+        case 16: apply_chunk_v2<R, 16>(xb, yb, m, p, spec, tw, W1, W2, 1, s); break;
+        case 32: apply_chunk_v2<R, 32>(xb, yb, m, p, spec, tw, W1, W2, 1, s); break;
+        case 64: apply_chunk_v2<R, 64>(xb, yb, m, p, spec, tw, W1, W2, 1, s); break;
+        case 128: apply_chunk_v2<R, 128>(xb, yb, m, p, spec, tw, W1, W2, 1, s); break;
+        case 256: apply_chunk_v2<R, 256>(xb, yb, m, p, spec, tw, W1, W2, 1, s); break;
+        case 512: apply_chunk_v2<R, 512>(xb, yb, m, p, spec, tw, W1, W2, 1, s); break;
+        default: spm_set_error("unsupported FFT length %d", L); return SPM_ERR_INVALID_ARG;
+        }
+    }
+    SPM_CUDA_TRY(cudaGetLastError());
+    return SPM_OK;
+}
+} // namespace
+
+extern "C" spm_status spm_apply_A_noalloc(spm_problem P, spm_prec prec, const void *x, void *y, int nrhs,
+                                          void *stream)
+{
+    if (!P) { spm_set_error("NULL problem"); return SPM_ERR_INVALID_ARG; }
+    if (prec != SPM_C128 && prec != SPM_C64) { spm_set_error("precision must be SPM_C128 or SPM_C64"); return SPM_ERR_INVALID_ARG; }
+    if (nrhs < 0) { spm_set_error("nrhs < 0"); return SPM_ERR_INVALID_ARG; }
+    if (nrhs > 0 && (!x || !y)) { spm_set_error("NULL buffer"); return SPM_ERR_INVALID_ARG; }
+    if (nrhs > 0 && x == y) { spm_set_error("input and output alias"); return SPM_ERR_INVALID_ARG; }
+    if (nrhs == 0) return SPM_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    return prec == SPM_C128 ? apply_A_noalloc_typed<double>(P, x, y, nrhs, s)
+                            : apply_A_noalloc_typed<float>(P, x, y, nrhs, s);
 }
