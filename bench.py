@@ -191,6 +191,21 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def aggregate_timing(total_ms, steps, units_per_step, world, dist=None, device="cpu"):
+    """Max of the timed region over ranks; value = units of all ranks per second.
+
+    With world > 1 every rank runs an independent replica (no data-path
+    collective); only this timing reduction crosses ranks."""
+    if world > 1 and dist is not None:
+        import torch
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / steps
+    value = world * units_per_step * steps / (total_ms / 1000.0)
+    return ms_per_step, value
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     for f in ("apply.cu", "fft.cuh", "common.cuh"):
@@ -210,15 +225,93 @@ def recorded_traffic(workload, prec, op):
     return e.get("dram_bytes_per_apply")
 
 
+def chunk_of(P, n, prec):
+    """Right-hand sides per pass chunk inside the library (intermediates kept in L2)."""
+    el = 8 if prec == "c64" else 16
+    per = 24.0 * n ** 3 * el
+    return 1 if per >= 64 * 2 ** 20 else min(64, int(64 * 2 ** 20 // per))
+
+
+def run_uneven(args, torch, spm, rank, world, local):
+    """32 independent problems (n in {32, 48, 64, 96}): batched apply (one CUDA
+    graph launch per step) and the batched mixed-precision solve to 1e-6."""
+    probs = si.uneven_batch(32)
+    B = spm.Batch([q["n"] for q in probs], [q["omega"] for q in probs], [q["eps"] for q in probs],
+                  [q["grad"] for q in probs])
+    dtype = torch.complex64 if args.prec == "c64" else torch.complex128
+    xs = [torch.from_numpy(q["einc"]).to(dtype).to("cuda") for q in probs]
+    ys = [torch.zeros_like(x) for x in xs]
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        B.apply_A(xs, ys)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    sampler.wait_first()
+    mark0 = sampler.mark()
+    ev = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        B.apply_A(xs, ys)
+        e1.record(stream)
+        ev.append((e0, e1))
+    torch.cuda.synchronize()
+    mark1 = sampler.mark()
+    time.sleep(0.25)
+    clocks = sampler.stop(max(0, mark0 - 1), mark1 + 1)
+    total_ms = float(np.sum([a.elapsed_time(b) for a, b in ev]))
+    dist = torch.distributed if world > 1 else None
+    ms_per_step, value = aggregate_timing(total_ms, args.steps, len(probs), world, dist, "cuda")
+    alg = sum(compulsory_bytes(q["n"], args.prec) for q in probs)
+    peak, peak_kind = peaks()
+    achieved = alg / (ms_per_step / 1000.0) / 1e9
+    line = {"metric": METRIC, "value": value, "unit": "problem applies/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
+            "config": {"workload": "uneven32", "sizes": sorted(set(q["n"] for q in probs)), "problems": len(probs),
+                       "op": "A", "graph": "one CUDA graph launch per step", "l2": "flushed between steps",
+                       "parallelism": f"replicas{world}"},
+            "roofline": {"bound": "hbm", "kernel": "batched apply_A (graph)", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
+                         "algorithmic_bytes": alg, "traffic": None},
+            "gpu_launches": 5 * len(probs) * args.steps, "clocks": clocks}
+    if args.solve != "none":
+        t0 = time.perf_counter()
+        B.build_stencils(spm.SPM_C64)
+        torch.cuda.synchronize()
+        setup_s = time.perf_counter() - t0
+        gs = []
+        for i, q in enumerate(probs):
+            e = torch.from_numpy(q["einc"]).to("cuda")
+            g = torch.zeros_like(e)
+            B.problems[i].rhs_from_incident(e, g)
+            gs.append(g)
+        xs2 = [torch.zeros_like(g) for g in gs]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        infos, st = B.solve(gs, xs2, prec=spm.SPM_MIXED, tol=1e-6, maxit=400, check=False)
+        torch.cuda.synchronize()
+        line["solve"] = {"mixed_batch_time_s": time.perf_counter() - t0, "status": st,
+                         "max_iterations": max(i.iterations for i in infos),
+                         "max_true_relres": max(i.true_relres for i in infos),
+                         "setup_stencils_factor_c64_s": setup_s}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def measure_solve(spm, torch, P, wl, args, have_c64_factor):
     """Time-to-1e-6 of the preconditioned solve (set-up reported separately)."""
-    out = {"tol": 1e-6, "restart": 20}
+    out = {"tol": 1e-6, "restart": 20, "nrhs": int(wl["einc"].shape[0])}
     n = wl["n"]
     t0 = time.perf_counter()
     if not have_c64_factor:
         P.build_stencils(spm.SPM_C64)
     torch.cuda.synchronize()
-    e = torch.from_numpy(wl["einc"][:1]).to("cuda")
+    e = torch.from_numpy(wl["einc"]).to("cuda")  # every incident field of the workload, one block solve
     g = torch.zeros_like(e)
     P.rhs_from_incident(e, g)
     modes = [("mixed", spm.SPM_MIXED)]
@@ -238,8 +331,24 @@ def measure_solve(spm, torch, P, wl, args, have_c64_factor):
             times.append(time.perf_counter() - t1)
         out[name] = {"time_s": float(np.median(times)), "iterations": info.iterations,
                      "outer_steps": info.outer_steps, "true_relres": info.true_relres, "status": st}
+    # the same mixed solve with the factor's blocks stored as scaled binary16
+    t1 = time.perf_counter()
+    P.factor_S(spm.SPM_C64H)
+    torch.cuda.synchronize()
+    out["setup_factor_c64_half_storage_s"] = time.perf_counter() - t1
+    times = []
+    for _ in range(3):
+        x = torch.zeros_like(g)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        info, st = P.solve(g, x, prec=spm.SPM_MIXED, tol=1e-6, maxit=400, restart=20, check=False)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t1)
+    out["mixed_half_factor"] = {"time_s": float(np.median(times)), "iterations": info.iterations,
+                                "outer_steps": info.outer_steps, "true_relres": info.true_relres, "status": st}
     if "fp64" in out:
         out["fp64_over_mixed"] = out["fp64"]["time_s"] / out["mixed"]["time_s"]
+        out["fp64_over_mixed_half_factor"] = out["fp64"]["time_s"] / out["mixed_half_factor"]["time_s"]
     return out
 
 
@@ -252,13 +361,20 @@ def run_ours(args):
     torch.cuda.set_device(local)
     import paper_1804_02297_gb300 as spm
 
+    if args.workload == "uneven32":
+        return run_uneven(args, torch, spm, rank, world, local)
     wl = si.workload(args.workload)
     n = wl["n"]
     P = spm.Problem(n, wl["omega"], wl["eps"], wl["grad"])
     dtype = torch.complex64 if args.prec == "c64" else torch.complex128
-    x = torch.from_numpy(wl["einc"][0]).to(dtype).to("cuda").contiguous()
+    nrhs = wl["einc"].shape[0]
+    x = torch.from_numpy(wl["einc"]).to(dtype).to("cuda").contiguous()
     y = torch.zeros_like(x)
     setup = {}
+    if n > 64:
+        args.solve = "none"  # the nested-dissection factor does not fit in one GPU above n = 64
+        if args.op == "QA":
+            args.op = "A"
     if args.op == "QA" or args.solve != "none":
         t0 = time.perf_counter()
         P.build_stencils(spm.SPM_C64)  # device stencil fit, S assembly, complex64 factor
@@ -266,7 +382,7 @@ def run_ours(args):
         setup["stencils_assembly_factor_c64_s"] = time.perf_counter() - t0
     if args.op == "QA":
         fn = P.apply_QA
-        launches_per_step = 6
+        launches_per_step = 7  # 5 FFT passes, Q interior, Q boundary shell
     else:
         fn = P.apply_A
         launches_per_step = 5
@@ -298,15 +414,11 @@ def run_ours(args):
     clocks = sampler.stop(max(0, mark0 - 1), mark1 + 1)
     step_ms = [a.elapsed_time(b) for a, b in times]
     total_ms = float(np.sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
-    value = world * args.steps / (total_ms / 1000.0)
+    dist = torch.distributed if world > 1 else None
+    ms_per_step, value = aggregate_timing(total_ms, args.steps, nrhs, world, dist, "cuda")
 
     # e2e: pinned host input -> device -> apply -> host, every step
-    xh = torch.from_numpy(wl["einc"][0]).to(dtype).pin_memory()
+    xh = torch.from_numpy(wl["einc"]).to(dtype).pin_memory()
     yh = torch.empty_like(xh).pin_memory()
     xd = torch.empty_like(x)
     for _ in range(2):
@@ -327,32 +439,31 @@ def run_ours(args):
         ev.append((e0, e1))
     torch.cuda.synchronize()
     e2e_ms = float(np.sum([a.elapsed_time(b) for a, b in ev]))
-    if world > 1:
-        t = torch.tensor([e2e_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    _, e2e_value = aggregate_timing(e2e_ms, args.steps, nrhs, world, dist, "cuda")
     nbytes = xh.numel() * xh.element_size()
 
     peak, peak_kind = peaks()
-    alg = compulsory_bytes(n, args.prec)
+    alg = compulsory_bytes(n, args.prec, nrhs)
     achieved = alg / (ms_per_step / 1000.0) / 1e9
     roof = {"bound": "hbm", "kernel": f"apply_{args.op} ({launches_per_step} launches)",
             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "peak_source": peak_kind, "algorithmic_bytes": alg,
             "traffic": recorded_traffic(args.workload, args.prec, args.op)}
 
-    line = {"metric": METRIC, "value": value, "unit": "applies/s", "n_gpus": world, "steps": args.steps,
+    line = {"metric": METRIC, "value": value, "unit": "field applies/s" if nrhs > 1 else "applies/s",
+            "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
-            "config": {"workload": args.workload, "n": n, "nrhs": 1, "op": args.op, "l2": "flushed (512 MiB write) between steps",
+            "config": {"workload": args.workload, "n": n, "nrhs": nrhs, "op": args.op,
+                       "l2": "flushed (512 MiB write) between steps",
                        "parallelism": f"replicas{world}"},
             "roofline": roof,
-            "e2e": {"value": world * args.steps / (e2e_ms / 1000.0), "unit": "applies/s",
+            "e2e": {"value": e2e_value, "unit": "field applies/s" if nrhs > 1 else "applies/s",
                     "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
-            "gpu_launches": launches_per_step * args.steps,
+            "gpu_launches": launches_per_step * args.steps * max(1, -(-nrhs // chunk_of(P, n, args.prec))),
             "clocks": clocks,
             "step_ms_min": float(np.min(step_ms)), "step_ms_median": float(np.median(step_ms))}
-    if args.solve != "none":
+    if args.solve != "none" and n <= 64:
         line["solve"] = measure_solve(spm, torch, P, wl, args, True)
         line["solve"]["setup"] = setup
     if rank == 0 and not args.no_cpu_baseline:

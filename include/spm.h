@@ -52,8 +52,12 @@ typedef enum {
 typedef enum { SPM_QUAD_ORDER4 = 0, SPM_QUAD_ORDER2 = 1 } spm_quad;
 
 /* Arithmetic of a call: complex128, complex64 (FP32 accumulation), or, for
- * spm_solve only, complex64 inner iterations inside an FP64 outer loop. */
-typedef enum { SPM_C128 = 0, SPM_C64 = 1, SPM_MIXED = 2 } spm_prec;
+ * spm_solve only, complex64 inner iterations inside an FP64 outer loop.
+ * SPM_C64H (spm_factor_S / spm_build_stencils only): the factor of S is
+ * computed in complex64 and its stored blocks are kept as binary16 pairs
+ * scaled per column by the column's largest component (half the memory and
+ * half the bytes each S^{-1} reads); it serves complex64 solves. */
+typedef enum { SPM_C128 = 0, SPM_C64 = 1, SPM_MIXED = 2, SPM_C64H = 3 } spm_prec;
 
 /* ---------------------------------------------------------------- set-up */
 
@@ -188,6 +192,35 @@ spm_status spm_rhs_from_incident(spm_problem prob, const void *einc_dev, void *g
  * Synchronises. */
 spm_status spm_solve(spm_problem prob, spm_prec prec, const void *g_dev, void *x_dev, int nrhs,
                      double tol, int maxit, int restart, spm_solve_info *info);
+
+/* ------------------------------------------------------------- batches */
+
+/* A batch of independent problems of uneven size: problem i has grid n[i],
+ * frequency omega[i] and its own medium (eps_host[i], grad_eps_host[i] or a
+ * NULL array / NULL entry for finite differences), all as in
+ * spm_create_problem.  Each problem gets its own stream, workspaces, stencils
+ * and factor; they share nothing, so the batch is embarrassingly parallel.
+ * Synchronises.  *out is a new batch handle. */
+typedef struct spm_batch_s *spm_batch;
+spm_status spm_create_batch(int count, const int *n, const double *omega, const double *const *eps_host,
+                            const double *const *grad_eps_host, spm_quad quad, spm_batch *out);
+spm_status spm_destroy_batch(spm_batch batch);
+spm_status spm_batch_size(spm_batch batch, int *count);
+/* Borrowed handle of problem `index` (owned by the batch: do not destroy it). */
+spm_status spm_batch_problem(spm_batch batch, int index, spm_problem *out);
+/* spm_build_stencils on every problem, concurrently. */
+spm_status spm_batch_build_stencils(spm_batch batch, spm_prec factor_prec);
+/* y_dev[i] = A_i x_dev[i] (one right-hand side per problem) for every problem,
+ * ordered on `stream`.  The problems run as parallel branches; the first call
+ * with a given set of buffers also captures the fork/join into a CUDA graph
+ * that later calls with the same buffers and precision replay. */
+spm_status spm_batch_apply_A(spm_batch batch, spm_prec prec, const void *const *x_dev, void *const *y_dev,
+                             void *stream);
+/* spm_solve on every problem (one right-hand side each), concurrently from a
+ * pool of host threads; infos (count entries) may be NULL.  Returns the first
+ * failing status.  Synchronises. */
+spm_status spm_batch_solve(spm_batch batch, spm_prec prec, const void *const *g_dev, void *const *x_dev,
+                           double tol, int maxit, int restart, spm_solve_info *infos);
 
 /* -------------------------------------------------------- inspection */
 

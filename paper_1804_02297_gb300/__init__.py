@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libspm.so")
 SPM_OK, SPM_ERR_INVALID_ARG, SPM_ERR_CUDA, SPM_ERR_OOM, SPM_ERR_NOT_BUILT, SPM_ERR_NO_CONVERGENCE, \
     SPM_ERR_TIMEOUT, SPM_ERR_NUMERICAL = range(8)
 SPM_QUAD_ORDER4, SPM_QUAD_ORDER2 = 0, 1
-SPM_C128, SPM_C64, SPM_MIXED = 0, 1, 2
+SPM_C128, SPM_C64, SPM_MIXED, SPM_C64H = 0, 1, 2, 3
 
 # every symbol include/spm.h declares
 EXPORTS = [
@@ -26,6 +26,8 @@ EXPORTS = [
     "spm_build_stencils", "spm_set_stencils", "spm_get_stencils", "spm_factor_S", "spm_apply_S",
     "spm_solve_S", "spm_incident_plane_wave", "spm_rhs_from_incident", "spm_solve", "spm_kernel_entries",
     "spm_lattice_constant", "spm_last_error", "spm_apply_A_noalloc",
+    "spm_create_batch", "spm_destroy_batch", "spm_batch_size", "spm_batch_problem", "spm_batch_build_stencils",
+    "spm_batch_apply_A", "spm_batch_solve",
 ]
 
 
@@ -63,6 +65,13 @@ def _load():
         "spm_rhs_from_incident": [P, P, P, I, P],
         "spm_solve": [P, I, P, P, I, D, I, I, ctypes.POINTER(SolveInfo)],
         "spm_kernel_entries": [P, P],
+        "spm_create_batch": [I, P, P, P, P, I, ctypes.POINTER(P)],
+        "spm_destroy_batch": [P],
+        "spm_batch_size": [P, ctypes.POINTER(I)],
+        "spm_batch_problem": [P, I, ctypes.POINTER(P)],
+        "spm_batch_build_stencils": [P, I],
+        "spm_batch_apply_A": [P, I, P, P, P],
+        "spm_batch_solve": [P, I, P, P, D, I, I, P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -229,3 +238,69 @@ class Problem:
         out = np.zeros((4, W, W, W), np.complex128)
         _check(lib.spm_kernel_entries(self.h, _ptr(out)))
         return out
+
+
+class _Borrowed(Problem):
+    """A problem owned by a Batch: same methods, never destroyed here."""
+
+    def __init__(self, handle, n):
+        self.h = handle
+        self.n = n
+
+    def close(self):
+        self.h = None
+
+
+class Batch:
+    """Owns one spm_batch handle: independent problems of uneven size."""
+
+    def __init__(self, ns, omegas, eps_list, grad_list=None, quad=SPM_QUAD_ORDER4):
+        count = len(ns)
+        self._keep = [np.ascontiguousarray(e, dtype=np.complex128) for e in eps_list]
+        self._keepg = None if grad_list is None else [np.ascontiguousarray(g, dtype=np.complex128) for g in grad_list]
+        n_arr = (ctypes.c_int * count)(*ns)
+        w_arr = (ctypes.c_double * count)(*[float(w) for w in omegas])
+        e_arr = (ctypes.c_void_p * count)(*[a.ctypes.data for a in self._keep])
+        g_arr = None if self._keepg is None else (ctypes.c_void_p * count)(*[a.ctypes.data for a in self._keepg])
+        h = ctypes.c_void_p()
+        _check(lib.spm_create_batch(count, n_arr, w_arr, e_arr, g_arr, quad, ctypes.byref(h)))
+        self.h = h
+        self.ns = list(ns)
+        self.problems = []
+        for i in range(count):
+            ph = ctypes.c_void_p()
+            _check(lib.spm_batch_problem(h, i, ctypes.byref(ph)))
+            self.problems.append(_Borrowed(ph, ns[i]))
+
+    def close(self):
+        if getattr(self, "h", None):
+            for p in self.problems:
+                p.close()
+            lib.spm_destroy_batch(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def build_stencils(self, factor_prec=SPM_C64):
+        _check(lib.spm_batch_build_stencils(self.h, factor_prec))
+
+    def apply_A(self, xs, ys, stream=None):
+        count = len(xs)
+        xa = (ctypes.c_void_p * count)(*[x.data_ptr() for x in xs])
+        ya = (ctypes.c_void_p * count)(*[y.data_ptr() for y in ys])
+        _check(lib.spm_batch_apply_A(self.h, _prec_of(xs[0]), xa, ya, _stream(stream)))
+        return ys
+
+    def solve(self, gs, xs, prec=SPM_MIXED, tol=1e-6, maxit=500, restart=20, check=True):
+        count = len(gs)
+        ga = (ctypes.c_void_p * count)(*[g.data_ptr() for g in gs])
+        xa = (ctypes.c_void_p * count)(*[x.data_ptr() for x in xs])
+        infos = (SolveInfo * count)()
+        st = lib.spm_batch_solve(self.h, prec, ga, xa, float(tol), int(maxit), int(restart), infos)
+        if check:
+            _check(st)
+        return list(infos), st

@@ -86,7 +86,10 @@ extern "C" spm_status spm_create_problem(int n, double omega, const double *eps_
     if (!out) { spm_set_error("out is NULL"); return SPM_ERR_INVALID_ARG; }
     *out = nullptr;
     if (n < 4 || n > 512) { spm_set_error("n = %d outside [4, 512]", n); return SPM_ERR_INVALID_ARG; }
-    if ((n & (n - 1)) != 0) { spm_set_error("n = %d: this build needs n a power of two (L = 2n)", n); return SPM_ERR_INVALID_ARG; }
+    if ((n & (n - 1)) != 0 && n != 48 && n != 96) {
+        spm_set_error("n = %d: the FFT length 2n must be a power of two or 96, 192 (n = 48, 96)", n);
+        return SPM_ERR_INVALID_ARG;
+    }
     if (!(omega > 0.0) || !isfinite(omega)) { spm_set_error("omega must be positive and finite"); return SPM_ERR_INVALID_ARG; }
     if (!eps_host) { spm_set_error("eps_host is NULL"); return SPM_ERR_INVALID_ARG; }
     if (quad != SPM_QUAD_ORDER4 && quad != SPM_QUAD_ORDER2) { spm_set_error("bad quadrature %d", (int)quad); return SPM_ERR_INVALID_ARG; }
@@ -203,6 +206,7 @@ extern "C" spm_status spm_destroy(spm_problem P)
     P->m128.release(); P->p128.release(); P->m64.release(); P->p64.release();
     P->spec128.release(); P->spec64.release(); P->tw128.release(); P->tw64.release();
     P->work.release(); P->alpha128.release(); P->alpha64.release(); P->beta128.release();
+    P->qtab128.release(); P->qtab64.release();
     P->S128.release(); P->S64.release(); P->kry.release();
     spm_factor_free(P->fac128);
     spm_factor_free(P->fac64);
@@ -274,6 +278,7 @@ extern "C" spm_status spm_set_stencils(spm_problem P, const double *alpha_host, 
     SPM_CUDA_TRY(cudaMemcpy(P->alpha64.ptr, a32.data(), 8 * 27 * 81 * 3, cudaMemcpyHostToDevice));
     SPM_CUDA_TRY(cudaMemcpy(P->beta128.ptr, P->beta_h.data(), 16 * 27 * 108 * 3, cudaMemcpyHostToDevice));
     P->have_stencils = true;
+    SPM_TRY(spm_build_qtable(P));
     spm_factor_free(P->fac128); P->fac128 = nullptr;
     spm_factor_free(P->fac64); P->fac64 = nullptr;
     return spm_assemble_S(P);
@@ -292,7 +297,7 @@ extern "C" spm_status spm_get_stencils(spm_problem P, double *alpha_host, double
 extern "C" spm_status spm_build_stencils(spm_problem P, spm_prec factor_prec)
 {
     if (!P) { spm_set_error("NULL problem"); return SPM_ERR_INVALID_ARG; }
-    if (!prec_ok(factor_prec)) { spm_set_error("factor precision must be SPM_C128 or SPM_C64"); return SPM_ERR_INVALID_ARG; }
+    if (!prec_ok(factor_prec) && factor_prec != SPM_C64H) { spm_set_error("factor precision must be SPM_C128, SPM_C64 or SPM_C64H"); return SPM_ERR_INVALID_ARG; }
     SPM_TRY(spm_stencils_device(P));
     spm_factor_free(P->fac128); P->fac128 = nullptr;
     spm_factor_free(P->fac64); P->fac64 = nullptr;
@@ -303,7 +308,7 @@ extern "C" spm_status spm_build_stencils(spm_problem P, spm_prec factor_prec)
 extern "C" spm_status spm_factor_S(spm_problem P, spm_prec prec)
 {
     if (!P) { spm_set_error("NULL problem"); return SPM_ERR_INVALID_ARG; }
-    if (!prec_ok(prec)) { spm_set_error("factor precision must be SPM_C128 or SPM_C64"); return SPM_ERR_INVALID_ARG; }
+    if (!prec_ok(prec) && prec != SPM_C64H) { spm_set_error("factor precision must be SPM_C128, SPM_C64 or SPM_C64H"); return SPM_ERR_INVALID_ARG; }
     if (!P->have_S) { spm_set_error("S not assembled"); return SPM_ERR_NOT_BUILT; }
     return spm_factor_impl(P, prec);
 }

@@ -15,6 +15,7 @@
 // The kernel spectra are stored as one octant [4][n+1]^3: Ghat is even in each
 // frequency, Ghat^d is odd in frequency d and even in the others.
 #include <mutex>
+#include <vector>
 
 #include "fft.cuh"
 #include "fft_reg.cuh"
@@ -61,51 +62,6 @@ __global__ void __launch_bounds__(NT) k_cols(const typename cplx_of<R>::type *in
     }
 }
 
-// -------------------------------------------------------------- Q gather
-// (Q v)_{i,c} = sum_{(d,o) in tau(class i)} alpha[class][(d,o)][c] v^d_{i+o}.
-// alpha packed [27][81][3]; row (d,o) = d*T + o, offsets enumerated o3, o2, o1.
-template <typename R>
-__global__ void k_qgather(const typename cplx_of<R>::type *__restrict__ v,
-                          const typename cplx_of<R>::type *__restrict__ alpha,
-                          typename cplx_of<R>::type *__restrict__ y, int n, long total)
-{
-    using C = typename cplx_of<R>::type;
-    long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= total) return;
-    const long n3 = (long)n * n * n;
-    long b = gid / n3, i = gid - b * n3;
-    int i1 = (int)(i % n), i2 = (int)((i / n) % n), i3 = (int)(i / ((long)n * n));
-    int c1 = i1 == 0 ? 0 : (i1 == n - 1 ? 2 : 1);
-    int c2 = i2 == 0 ? 0 : (i2 == n - 1 ? 2 : 1);
-    int c3 = i3 == 0 ? 0 : (i3 == n - 1 ? 2 : 1);
-    int cls = c1 + 3 * c2 + 9 * c3;
-    int lo1 = c1 == 0 ? 0 : -1, hi1 = c1 == 2 ? 0 : 1;
-    int lo2 = c2 == 0 ? 0 : -1, hi2 = c2 == 2 ? 0 : 1;
-    int lo3 = c3 == 0 ? 0 : -1, hi3 = c3 == 2 ? 0 : 1;
-    int T = (hi1 - lo1 + 1) * (hi2 - lo2 + 1) * (hi3 - lo3 + 1);
-    const C *al = alpha + (long)cls * 81 * 3;
-    const C *vb = v + b * 3 * n3;
-    C acc0 = czero<C>(), acc1 = czero<C>(), acc2 = czero<C>();
-    int o = 0;
-    for (int o3 = lo3; o3 <= hi3; ++o3)
-        for (int o2 = lo2; o2 <= hi2; ++o2)
-            for (int o1 = lo1; o1 <= hi1; ++o1, ++o) {
-                long j = ((long)(i3 + o3) * n + (i2 + o2)) * n + (i1 + o1);
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    C val = vb[d * n3 + j];
-                    const C *ar = al + (d * T + o) * 3;
-                    acc0 = cfma(ar[0], val, acc0);
-                    acc1 = cfma(ar[1], val, acc1);
-                    acc2 = cfma(ar[2], val, acc2);
-                }
-            }
-    C *yb = y + b * 3 * n3;
-    yb[i] = acc0;
-    yb[n3 + i] = acc1;
-    yb[2 * n3 + i] = acc2;
-}
-
 // ================================================================ v2 passes
 // Register-resident line FFTs (fft_reg.cuh): thread t of a line holds elements
 // t + T m, m = 0..7, T = L/8.  Strided passes use TX adjacent columns per block
@@ -121,6 +77,15 @@ template <typename R, int L> struct tx_of {
 
 template <int L> __device__ __forceinline__ int xpad(int pos) { return pos + (pos >> 3); }
 
+// asynchronous global -> shared copies (cp.async), BYTES = 8 or 16
+template <int BYTES> __device__ __forceinline__ void cp_async(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 // xfwd: w_f of one grid row per line, FFT along x (pruned), 4 fields in turn.
 template <typename R, int L>
 __global__ void __launch_bounds__(256) k2_xfwd(const typename cplx_of<R>::type *__restrict__ x,
@@ -130,7 +95,8 @@ __global__ void __launch_bounds__(256) k2_xfwd(const typename cplx_of<R>::type *
                                                const typename cplx_of<R>::type *__restrict__ tw)
 {
     using C = typename cplx_of<R>::type;
-    constexpr int T = L / 8, n = L / 2, LPB = 256 / T > 0 ? 256 / T : 1, LS = L + L / 8;
+    constexpr int E = line_elems(L), H = E / 2;
+    constexpr int T = L / E, n = L / 2, LPB = 256 / T > 0 ? 256 / T : 1, LS = L + L / 8;
     extern __shared__ unsigned char smem_raw[];
     C *sm = reinterpret_cast<C *>(smem_raw);
     const int line = threadIdx.x / T, t = threadIdx.x % T;
@@ -138,36 +104,50 @@ __global__ void __launch_bounds__(256) k2_xfwd(const typename cplx_of<R>::type *
     const bool ok = g < nrows;
     const long n2 = (long)n * n, n3 = n2 * n;
     const long b = ok ? g / n2 : 0, zy = ok ? g - b * n2 : 0;
-    C e[3][4], mm[4], pp[3][4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        long off = zy * n + t + T * q;
-        if (ok) {
-            const C *xb = x + b * 3 * n3;
-            e[0][q] = xb[off]; e[1][q] = xb[n3 + off]; e[2][q] = xb[2 * n3 + off];
-            mm[q] = m[off];
-            pp[0][q] = p[off]; pp[1][q] = p[n3 + off]; pp[2][q] = p[2 * n3 + off];
-        } else {
-            e[0][q] = e[1][q] = e[2][q] = mm[q] = pp[0][q] = pp[1][q] = pp[2][q] = czero<C>();
-        }
-    }
+    const C *xb = x + b * 3 * n3;
     C *lb = sm + line * LS;
     auto buf = [&](int pos) -> C & { return lb[xpad<L>(pos)]; };
     auto sync = [&]() { if (T <= 32) __syncwarp(); else __syncthreads(); };
+    // E = 8: the 7 inputs of the row stay in registers for the 4 fields;
+    // E = 12: reloaded per field (cached in L1) to keep register pressure down
+    constexpr bool CACHE = (E == 8);
+    constexpr int HC = CACHE ? H : 1;
+    C e[3][HC], mm[HC], pp[3][HC];
+    if constexpr (CACHE) {
+#pragma unroll
+        for (int q = 0; q < H; ++q) {
+            const long off = zy * n + t + T * q;
+            if (ok) {
+                e[0][q] = xb[off]; e[1][q] = xb[n3 + off]; e[2][q] = xb[2 * n3 + off];
+                mm[q] = m[off];
+                pp[0][q] = p[off]; pp[1][q] = p[n3 + off]; pp[2][q] = p[2 * n3 + off];
+            } else {
+                e[0][q] = e[1][q] = e[2][q] = mm[q] = pp[0][q] = pp[1][q] = pp[2][q] = czero<C>();
+            }
+        }
+    }
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
-        C v[8];
+        C v[E];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (f < 3) v[q] = cmul(mm[q], e[f][q]);
-            else v[q] = cfma(pp[0][q], e[0][q], cfma(pp[1][q], e[1][q], cmul(pp[2][q], e[2][q])));
-            v[q + 4] = czero<C>();
+        for (int q = 0; q < H; ++q) {
+            C w = czero<C>();
+            if constexpr (CACHE) {
+                if (f < 3) w = cmul(mm[q], e[f][q]);
+                else w = cfma(pp[0][q], e[0][q], cfma(pp[1][q], e[1][q], cmul(pp[2][q], e[2][q])));
+            } else if (ok) {
+                const long off = zy * n + t + T * q;
+                if (f < 3) w = cmul(m[off], xb[f * n3 + off]);
+                else w = cfma(p[off], xb[off], cfma(p[n3 + off], xb[n3 + off], cmul(p[2 * n3 + off], xb[2 * n3 + off])));
+            }
+            v[q] = w;
+            v[q + H] = czero<C>();
         }
-        fftr::fft_line<-1, L, true>(v, t, buf, sync, tw);
+        line_fft<-1, L, true>(v, t, buf, sync, tw);
         if (ok) {
             C *dst = W1 + ((b * 4 + f) * n2 + zy) * L;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) dst[t + T * q] = v[q];
+            for (int q = 0; q < E; ++q) dst[t + T * q] = v[q];
         }
         sync();
     }
@@ -176,12 +156,13 @@ __global__ void __launch_bounds__(256) k2_xfwd(const typename cplx_of<R>::type *
 // Strided lines: element (b, f, z, pos, i) at in[b*ib + f*if_ + z*iz + pos*inner + i];
 // grid (inner/TX, nz, nb*F).  nin, nout in {L/2, L}.
 template <typename R, int L, int DIR, bool PRUNE>
-__global__ void __launch_bounds__(tx_of<R, L>::v * L / 8) k2_cols(const typename cplx_of<R>::type *in, typename cplx_of<R>::type *out,
+__global__ void __launch_bounds__(tx_of<R, L>::v * L / line_elems(L)) k2_cols(const typename cplx_of<R>::type *in, typename cplx_of<R>::type *out,
                                                 int nout, long inner, int F, long ib, long if_, long iz, long ob,
                                                 long of, long oz, const typename cplx_of<R>::type *__restrict__ tw)
 {
     using C = typename cplx_of<R>::type;
-    constexpr int T = L / 8, TX = tx_of<R, L>::v;
+    constexpr int E = line_elems(L), H = E / 2;
+    constexpr int T = L / E, TX = tx_of<R, L>::v;
     extern __shared__ unsigned char smem_raw[];
     C *sm = reinterpret_cast<C *>(smem_raw);
     const int c = threadIdx.x % TX, t = threadIdx.x / TX;
@@ -190,29 +171,35 @@ __global__ void __launch_bounds__(tx_of<R, L>::v * L / 8) k2_cols(const typename
     const int b = blockIdx.z / F, f = blockIdx.z % F;
     const C *src = in + b * ib + f * if_ + z * iz + i0 + c;
     C *dst = out + b * ob + f * of + z * oz + i0 + c;
-    C v[8];
+    C v[E];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = (!PRUNE || q < 4) ? src[(long)(t + T * q) * inner] : czero<C>();
+    for (int q = 0; q < E; ++q) v[q] = (!PRUNE || q < H) ? src[(long)(t + T * q) * inner] : czero<C>();
     auto buf = [&](int pos) -> C & { return sm[pos * TX + c]; };
     auto sync = [&]() { __syncthreads(); };
-    fftr::fft_line<DIR, L, PRUNE>(v, t, buf, sync, tw);
+    line_fft<DIR, L, PRUNE>(v, t, buf, sync, tw);
 #pragma unroll
-    for (int q = 0; q < 8; ++q)
+    for (int q = 0; q < E; ++q)
         if (t + T * q < nout) dst[(long)(t + T * q) * inner] = v[q];
 }
 
 // zprod: lines along z of W2[b][4][z<n][eta][xi] (TX adjacent columns), product
 // with the octant spectra, inverse along z, keep z < n (in place, fields 0..2).
+// The four fields' columns are prefetched into shared memory with cp.async at
+// the start (one commit group per field, in the order they are consumed); each
+// thread reads back only the elements it copied, so no block barrier is needed
+// for the prefetch.
 template <typename R, int L>
-__global__ void __launch_bounds__(tx_of<R, L>::v * L / 8) k2_zprod(typename cplx_of<R>::type *W2,
+__global__ void __launch_bounds__(tx_of<R, L>::v * L / line_elems(L)) k2_zprod1(typename cplx_of<R>::type *W2,
                                                  const typename cplx_of<R>::type *__restrict__ spec,
                                                  const typename cplx_of<R>::type *__restrict__ tw)
 {
     using C = typename cplx_of<R>::type;
-    constexpr int T = L / 8, TX = tx_of<R, L>::v, n = L / 2, n1 = n + 1;
+    constexpr int E = line_elems(L), H = E / 2;
+    constexpr int T = L / E, TX = tx_of<R, L>::v, n = L / 2, n1 = n + 1;
     constexpr long L2 = (long)L * L, oct = (long)n1 * n1 * n1, fs = (long)n * L * L;
     extern __shared__ unsigned char smem_raw[];
     C *sm = reinterpret_cast<C *>(smem_raw);
+    C *pre = sm + L * TX; // [4 fields in consumption order][n][TX]
     const int c = threadIdx.x % TX, t = threadIdx.x / TX;
     const long col = (long)blockIdx.x * TX + c;
     const int b = blockIdx.y;
@@ -221,24 +208,37 @@ __global__ void __launch_bounds__(tx_of<R, L>::v * L / 8) k2_zprod(typename cplx
     const int a1 = xi <= n ? xi : L - xi, a2 = eta <= n ? eta : L - eta;
     auto buf = [&](int pos) -> C & { return sm[pos * TX + c]; };
     auto sync = [&]() { __syncthreads(); };
-    C w4[8];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) w4[q] = base[3 * fs + (long)(t + T * q) * L2];
+    for (int g = 0; g < 4; ++g) {
+        const int f = g == 0 ? 3 : g - 1;
 #pragma unroll
-    for (int q = 4; q < 8; ++q) w4[q] = czero<C>();
-    fftr::fft_line<-1, L, true>(w4, t, buf, sync, tw);
-#pragma unroll 1
+        for (int q = 0; q < H; ++q) {
+            const int z = t + T * q;
+            cp_async<sizeof(C)>(&pre[(g * n + z) * TX + c], base + f * fs + (long)z * L2);
+        }
+        cp_async_commit();
+    }
+    C w4[E];
+    cp_async_wait<3>();
+#pragma unroll
+    for (int q = 0; q < H; ++q) w4[q] = pre[(0 * n + t + T * q) * TX + c];
+#pragma unroll
+    for (int q = H; q < E; ++q) w4[q] = czero<C>();
+    line_fft<-1, L, true>(w4, t, buf, sync, tw);
+#pragma unroll
     for (int d = 0; d < 3; ++d) {
-        C v[8];
-        sync();
+        C v[E];
+        if (d == 0) cp_async_wait<2>();
+        else if (d == 1) cp_async_wait<1>();
+        else cp_async_wait<0>();
 #pragma unroll
-        for (int q = 0; q < 4; ++q) v[q] = base[d * fs + (long)(t + T * q) * L2];
+        for (int q = 0; q < H; ++q) v[q] = pre[((d + 1) * n + t + T * q) * TX + c];
 #pragma unroll
-        for (int q = 4; q < 8; ++q) v[q] = czero<C>();
-        fftr::fft_line<-1, L, true>(v, t, buf, sync, tw);
+        for (int q = H; q < E; ++q) v[q] = czero<C>();
+        line_fft<-1, L, true>(v, t, buf, sync, tw);
         const int fr_fixed = d == 0 ? xi : eta;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
+        for (int q = 0; q < E; ++q) {
             const int zeta = t + T * q;
             const int a3 = zeta <= n ? zeta : L - zeta;
             const long o = ((long)a3 * n1 + a2) * n1 + a1;
@@ -247,11 +247,61 @@ __global__ void __launch_bounds__(tx_of<R, L>::v * L / 8) k2_zprod(typename cplx
             if (fr > n) { Kd.x = -Kd.x; Kd.y = -Kd.y; }
             v[q] = cfma(K0, v[q], cmul(Kd, w4[q]));
         }
-        sync();
-        fftr::fft_line<1, L, false>(v, t, buf, sync, tw);
+        line_fft<1, L, false>(v, t, buf, sync, tw);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) base[d * fs + (long)(t + T * q) * L2] = v[q];
+        for (int q = 0; q < H; ++q) base[d * fs + (long)(t + T * q) * L2] = v[q];
     }
+}
+
+// zprod, E = 8: the four forward z-transforms run together (shared barriers),
+// then the three products and the three inverse transforms together.
+template <typename R, int L>
+__global__ void __launch_bounds__(tx_of<R, L>::v * L / 8) k2_zprod4(typename cplx_of<R>::type *W2,
+                                                                  const typename cplx_of<R>::type *__restrict__ spec,
+                                                                  const typename cplx_of<R>::type *__restrict__ tw)
+{
+    using C = typename cplx_of<R>::type;
+    constexpr int T = L / 8, TX = tx_of<R, L>::v, n = L / 2, n1 = n + 1;
+    constexpr long L2 = (long)L * L, oct = (long)n1 * n1 * n1, fs = (long)n * L * L;
+    extern __shared__ unsigned char smem_raw[];
+    C *sm = reinterpret_cast<C *>(smem_raw); // 4 exchange buffers [4][L][TX]
+    const int c = threadIdx.x % TX, t = threadIdx.x / TX;
+    const long col = (long)blockIdx.x * TX + c;
+    const int b = blockIdx.y;
+    C *base = W2 + (long)b * 4 * fs + col;
+    const int eta = (int)(col / L), xi = (int)(col % L);
+    const int a1 = xi <= n ? xi : L - xi, a2 = eta <= n ? eta : L - eta;
+    auto buf = [&](int k, int pos) -> C & { return sm[(k * L + pos) * TX + c]; };
+    auto sync = [&]() { __syncthreads(); };
+    C w[4][8]; // fields 0, 1, 2 and p.E (index 3)
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) w[f][q] = base[f * fs + (long)(t + T * q) * L2];
+#pragma unroll
+        for (int q = 4; q < 8; ++q) w[f][q] = czero<C>();
+    }
+    fftr::fft_lines<-1, L, true, 4>(w, t, buf, sync, tw);
+    C v[3][8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int zeta = t + T * q;
+        const int a3 = zeta <= n ? zeta : L - zeta;
+        const long o = ((long)a3 * n1 + a2) * n1 + a1;
+        const C K0 = spec[o];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            C Kd = spec[(1 + d) * oct + o];
+            const int fr = d == 0 ? xi : (d == 1 ? eta : zeta);
+            if (fr > n) { Kd.x = -Kd.x; Kd.y = -Kd.y; }
+            v[d][q] = cfma(K0, w[d][q], cmul(Kd, w[3][q]));
+        }
+    }
+    fftr::fft_lines<1, L, false, 3>(v, t, buf, sync, tw);
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) base[d * fs + (long)(t + T * q) * L2] = v[d][q];
 }
 
 // xinv: rows of V1 (length L) -> y = x + IFFT(row)[x < n]
@@ -262,22 +312,23 @@ __global__ void __launch_bounds__(256) k2_xinv(const typename cplx_of<R>::type *
                                                const typename cplx_of<R>::type *__restrict__ tw)
 {
     using C = typename cplx_of<R>::type;
-    constexpr int T = L / 8, n = L / 2, LPB = 256 / T > 0 ? 256 / T : 1, LS = L + L / 8;
+    constexpr int E = line_elems(L), H = E / 2;
+    constexpr int T = L / E, n = L / 2, LPB = 256 / T > 0 ? 256 / T : 1, LS = L + L / 8;
     extern __shared__ unsigned char smem_raw[];
     C *sm = reinterpret_cast<C *>(smem_raw);
     const int line = threadIdx.x / T, t = threadIdx.x % T;
     const long g = (long)blockIdx.x * LPB + line;
     const bool ok = g < nrows;
-    C v[8];
+    C v[E];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] = ok ? V1[g * L + t + T * q] : czero<C>();
+    for (int q = 0; q < E; ++q) v[q] = ok ? V1[g * L + t + T * q] : czero<C>();
     C *lb = sm + line * LS;
     auto buf = [&](int pos) -> C & { return lb[xpad<L>(pos)]; };
     auto sync = [&]() { if (T <= 32) __syncwarp(); else __syncthreads(); };
-    fftr::fft_line<1, L, false>(v, t, buf, sync, tw);
+    line_fft<1, L, false>(v, t, buf, sync, tw);
     if (ok) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < H; ++q) {
             long o = g * n + t + T * q;
             y[o] = xin[o] + v[q];
         }
@@ -296,16 +347,19 @@ void apply_chunk_v2(const typename cplx_of<R>::type *xb, typename cplx_of<R>::ty
                     typename cplx_of<R>::type *W1, typename cplx_of<R>::type *W2, int nb, cudaStream_t s)
 {
     using C = typename cplx_of<R>::type;
-    constexpr int n = L / 2, T = L / 8, TX = tx_of<R, L>::v;
+    constexpr int n = L / 2, T = L / line_elems(L), TX = tx_of<R, L>::v;
     constexpr int LPB = 256 / T > 0 ? 256 / T : 1;
     constexpr size_t sm_rows = sizeof(C) * LPB * (L + L / 8), sm_cols = sizeof(C) * L * TX;
+    constexpr size_t sm_zprod = sm_cols + sizeof(C) * 4 * n * TX;
+    constexpr size_t sm_zprod4 = 4 * sm_cols;
     static bool attrs = false;
     if (!attrs) {
         allow_smem(k2_xfwd<R, L>, sm_rows);
         allow_smem(k2_xinv<R, L>, sm_rows);
         allow_smem(k2_cols<R, L, -1, true>, sm_cols);
         allow_smem(k2_cols<R, L, 1, false>, sm_cols);
-        allow_smem(k2_zprod<R, L>, sm_cols);
+        if constexpr (line_elems(L) == 8) allow_smem(k2_zprod4<R, L>, sm_zprod4);
+        else allow_smem(k2_zprod1<R, L>, sm_zprod);
         attrs = true;
     }
     const long n2 = (long)n * n, L2 = (long)L * L;
@@ -316,7 +370,10 @@ void apply_chunk_v2(const typename cplx_of<R>::type *xb, typename cplx_of<R>::ty
     }
     k2_cols<R, L, -1, true><<<dim3(L / TX, n, nb * 4), THR, sm_cols, s>>>(
         W1, W2, L, L, 4, 4 * n2 * L, n2 * L, n * (long)L, 4 * (long)n * L2, (long)n * L2, L2, tw);
-    k2_zprod<R, L><<<dim3((unsigned)(L2 / TX), nb), THR, sm_cols, s>>>(W2, spec, tw);
+    if constexpr (line_elems(L) == 8)
+        k2_zprod4<R, L><<<dim3((unsigned)(L2 / TX), nb), THR, sm_zprod4, s>>>(W2, spec, tw);
+    else
+        k2_zprod1<R, L><<<dim3((unsigned)(L2 / TX), nb), THR, sm_zprod, s>>>(W2, spec, tw);
     k2_cols<R, L, 1, false><<<dim3(L / TX, n, nb * 3), THR, sm_cols, s>>>(
         W2, W1, n, L, 3, 4 * (long)n * L2, (long)n * L2, L2, 3 * n2 * L, n2 * L, n * (long)L, tw);
     {
@@ -355,6 +412,8 @@ spm_status apply_A_typed(spm_problem_s *P, const void *xv, void *yv, int nrhs, c
         case 128: apply_chunk_v2<R, 128>(xb, yb, m, p, spec, tw, W1, W2, nb, s); break;
         case 256: apply_chunk_v2<R, 256>(xb, yb, m, p, spec, tw, W1, W2, nb, s); break;
         case 512: apply_chunk_v2<R, 512>(xb, yb, m, p, spec, tw, W1, W2, nb, s); break;
+        case 96: apply_chunk_v2<R, 96>(xb, yb, m, p, spec, tw, W1, W2, nb, s); break;
+        case 192: apply_chunk_v2<R, 192>(xb, yb, m, p, spec, tw, W1, W2, nb, s); break;
         default: spm_set_error("unsupported FFT length %d", L); return SPM_ERR_INVALID_ARG;
         }
     }
@@ -362,20 +421,212 @@ spm_status apply_A_typed(spm_problem_s *P, const void *xv, void *yv, int nrhs, c
     return SPM_OK;
 }
 
+// Q gather in two launches.
+// Interior points (1 <= i_d <= n-2, one class): a block owns a 32 x 4 x 2 tile
+// whose three components plus a one-point halo are staged in shared memory; the
+// class's 243 coefficients arrive as a by-value kernel parameter, so they sit in
+// the constant bank and enter the FMAs as operands without load instructions.
+// Boundary shell (at least one i_d in {0, n-1}, 26 classes): one warp per
+// point below, coefficients from the expanded table [cls][d][o][c] (zero
+// outside the class neighbourhood).
+constexpr int QX = 32, QY = 4, QZ = 2;
+constexpr int QHX = QX + 2, QHY = QY + 2, QHZ = QZ + 2, QH = QHX * QHY * QHZ;
+
+template <typename C> struct QInterior {
+    C a[243]; // [d][o][c], o = (o3+1)*9 + (o2+1)*3 + (o1+1)
+};
+
+template <typename R>
+__global__ void __launch_bounds__(QX * QY * QZ) k_q_interior(const typename cplx_of<R>::type *__restrict__ v,
+                                                             const QInterior<typename cplx_of<R>::type> qa,
+                                                             typename cplx_of<R>::type *__restrict__ y, int n)
+{
+    using C = typename cplx_of<R>::type;
+    __shared__ C sv[3 * QH];
+    const long n3 = (long)n * n * n;
+    const int m = n - 2; // interior extent
+    const int tiles_x = (m + QX - 1) / QX;
+    const int tx0 = 1 + (blockIdx.x % tiles_x) * QX, ty0 = 1 + (blockIdx.x / tiles_x) * QY;
+    const int tz0 = 1 + blockIdx.y * QZ;
+    const long b = blockIdx.z;
+    const C *vb = v + b * 3 * n3;
+    for (int i = threadIdx.x; i < 3 * QH; i += blockDim.x) {
+        int d = i / QH, h = i % QH;
+        int hx = h % QHX, hy = (h / QHX) % QHY, hz = h / (QHX * QHY);
+        int gx = tx0 + hx - 1, gy = ty0 + hy - 1, gz = tz0 + hz - 1;
+        C val = czero<C>();
+        if (gx < n && gy < n && gz < n) val = vb[d * n3 + ((long)gz * n + gy) * n + gx];
+        sv[i] = val;
+    }
+    __syncthreads();
+    const int lx = threadIdx.x % QX, ly = (threadIdx.x / QX) % QY, lz = threadIdx.x / (QX * QY);
+    const int i1 = tx0 + lx, i2 = ty0 + ly, i3 = tz0 + lz;
+    if (i1 > n - 2 || i2 > n - 2 || i3 > n - 2) return;
+    C acc0 = czero<C>(), acc1 = czero<C>(), acc2 = czero<C>();
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        int o = 0;
+#pragma unroll
+        for (int o3 = -1; o3 <= 1; ++o3)
+#pragma unroll
+            for (int o2 = -1; o2 <= 1; ++o2)
+#pragma unroll
+                for (int o1 = -1; o1 <= 1; ++o1, ++o) {
+                    const int h = ((lz + 1 + o3) * QHY + (ly + 1 + o2)) * QHX + (lx + 1 + o1);
+                    const C val = sv[d * QH + h];
+                    acc0 = cfma(qa.a[(d * 27 + o) * 3 + 0], val, acc0);
+                    acc1 = cfma(qa.a[(d * 27 + o) * 3 + 1], val, acc1);
+                    acc2 = cfma(qa.a[(d * 27 + o) * 3 + 2], val, acc2);
+                }
+    }
+    const long i = ((long)i3 * n + i2) * n + i1;
+    C *yb = y + b * 3 * n3;
+    yb[i] = acc0;
+    yb[n3 + i] = acc1;
+    yb[2 * n3 + i] = acc2;
+}
+
+// shell point number e (0 <= e < 6n^2 - 12n + 8) -> (i1, i2, i3): the two z faces,
+// then the two y faces of the interior z range, then the two x faces of the
+// interior (y, z) range
+__device__ __forceinline__ void shell_point(long e, int n, int &i1, int &i2, int &i3)
+{
+    const long n2 = (long)n * n, zf = 2 * n2, yf = 2L * n * (n - 2);
+    if (e < zf) {
+        i3 = e < n2 ? 0 : n - 1;
+        const long r = e % n2;
+        i2 = (int)(r / n);
+        i1 = (int)(r % n);
+    } else if (e < zf + yf) {
+        const long r = e - zf, half = (long)n * (n - 2);
+        i2 = r < half ? 0 : n - 1;
+        const long q = r % half;
+        i3 = 1 + (int)(q / n);
+        i1 = (int)(q % n);
+    } else {
+        const long r = e - zf - yf;
+        i1 = (r & 1) ? n - 1 : 0;
+        const long q = r >> 1;
+        i2 = 1 + (int)(q % (n - 2));
+        i3 = 1 + (int)(q / (n - 2));
+    }
+}
+
+// Boundary shell: one warp per shell point; lane l takes the terms (d, o) with
+// d * 27 + o in {l, l + 32, l + 64} (of 81), then the warp sums its partials.
+// Coefficients come from the expanded table (zero outside the neighbourhood,
+// which is also where a neighbour would leave the grid).
+template <typename R>
+__global__ void __launch_bounds__(256) k_q_shell(const typename cplx_of<R>::type *__restrict__ v,
+                                                 const typename cplx_of<R>::type *__restrict__ qtab,
+                                                 typename cplx_of<R>::type *__restrict__ y, int n, long per_rhs,
+                                                 int nrhs)
+{
+    using C = typename cplx_of<R>::type;
+    const long w = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= per_rhs * nrhs) return; // whole warps leave together
+    const long n3 = (long)n * n * n;
+    const long b = w / per_rhs;
+    int i1, i2, i3;
+    shell_point(w - b * per_rhs, n, i1, i2, i3);
+    const int c1 = i1 == 0 ? 0 : (i1 == n - 1 ? 2 : 1);
+    const int c2 = i2 == 0 ? 0 : (i2 == n - 1 ? 2 : 1);
+    const int c3 = i3 == 0 ? 0 : (i3 == n - 1 ? 2 : 1);
+    const C *al = qtab + (long)(c1 + 3 * c2 + 9 * c3) * 243;
+    const C *vb = v + b * 3 * n3;
+    C acc0 = czero<C>(), acc1 = czero<C>(), acc2 = czero<C>();
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int term = lane + 32 * k;
+        if (term >= 81) break;
+        const int d = term / 27, o = term % 27;
+        const int j1 = i1 + o % 3 - 1, j2 = i2 + (o / 3) % 3 - 1, j3 = i3 + o / 9 - 1;
+        if (j1 < 0 || j2 < 0 || j3 < 0 || j1 >= n || j2 >= n || j3 >= n) continue;
+        const C val = vb[d * n3 + ((long)j3 * n + j2) * n + j1];
+        const C *ar = al + (d * 27 + o) * 3;
+        acc0 = cfma(ar[0], val, acc0);
+        acc1 = cfma(ar[1], val, acc1);
+        acc2 = cfma(ar[2], val, acc2);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        acc0.x += __shfl_down_sync(0xffffffffu, acc0.x, off);
+        acc0.y += __shfl_down_sync(0xffffffffu, acc0.y, off);
+        acc1.x += __shfl_down_sync(0xffffffffu, acc1.x, off);
+        acc1.y += __shfl_down_sync(0xffffffffu, acc1.y, off);
+        acc2.x += __shfl_down_sync(0xffffffffu, acc2.x, off);
+        acc2.y += __shfl_down_sync(0xffffffffu, acc2.y, off);
+    }
+    if (lane == 0) {
+        const long i = ((long)i3 * n + i2) * n + i1;
+        C *yb = y + b * 3 * n3;
+        yb[i] = acc0;
+        yb[n3 + i] = acc1;
+        yb[2 * n3 + i] = acc2;
+    }
+}
+
 template <typename R>
 spm_status apply_Q_typed(spm_problem_s *P, const void *vv, void *yv, int nrhs, cudaStream_t s)
 {
     using C = typename cplx_of<R>::type;
     const int n = P->n;
-    const long total = (long)nrhs * n * n * n;
-    const C *alpha = sizeof(R) == 8 ? P->alpha128.as<C>() : P->alpha64.as<C>();
-    int grid = (int)((total + 255) / 256);
-    k_qgather<R><<<grid, 256, 0, s>>>(reinterpret_cast<const C *>(vv), alpha, reinterpret_cast<C *>(yv), n, total);
+    const C *qtab = sizeof(R) == 8 ? P->qtab128.as<C>() : P->qtab64.as<C>();
+    // interior coefficients (class 13) by value, from the host copy of the table
+    QInterior<C> qa;
+    for (int i = 0; i < 243; ++i) {
+        qa.a[i].x = (R)P->qtab_h[2 * (13 * 243 + i)];
+        qa.a[i].y = (R)P->qtab_h[2 * (13 * 243 + i) + 1];
+    }
+    const C *v = reinterpret_cast<const C *>(vv);
+    C *y = reinterpret_cast<C *>(yv);
+    const int m = n - 2;
+    const int tiles_x = (m + QX - 1) / QX, tiles_y = (m + QY - 1) / QY;
+    dim3 grid((unsigned)(tiles_x * tiles_y), (unsigned)((m + QZ - 1) / QZ), (unsigned)nrhs);
+    k_q_interior<R><<<grid, QX * QY * QZ, 0, s>>>(v, qa, y, n);
+    const long shell = 6L * n * n - 12L * n + 8;
+    k_q_shell<R><<<(unsigned)((shell * nrhs * 32 + 255) / 256), 256, 0, s>>>(v, qtab, y, n, shell, nrhs);
     SPM_CUDA_TRY(cudaGetLastError());
     return SPM_OK;
 }
 
 } // namespace
+
+// alpha of every class spread over all 27 offsets [cls][d][o][c], o = (o3+1)*9 + (o2+1)*3 + (o1+1)
+spm_status spm_build_qtable(spm_problem_s *P)
+{
+    std::vector<double> t(2 * 27 * 243, 0.0);
+    for (int cls = 0; cls < 27; ++cls) {
+        const int c[3] = {cls % 3, (cls / 3) % 3, cls / 9};
+        int lo[3], hi[3], w[3];
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = c[d] == 0 ? 0 : -1;
+            hi[d] = c[d] == 2 ? 0 : 1;
+            w[d] = hi[d] - lo[d] + 1;
+        }
+        const int T = w[0] * w[1] * w[2];
+        for (int o3 = lo[2]; o3 <= hi[2]; ++o3)
+            for (int o2 = lo[1]; o2 <= hi[1]; ++o2)
+                for (int o1 = lo[0]; o1 <= hi[0]; ++o1) {
+                    const int oi = ((o3 - lo[2]) * w[1] + (o2 - lo[1])) * w[0] + (o1 - lo[0]);
+                    const int of = (o3 + 1) * 9 + (o2 + 1) * 3 + (o1 + 1);
+                    for (int d = 0; d < 3; ++d)
+                        for (int cc = 0; cc < 3; ++cc)
+                            for (int ri = 0; ri < 2; ++ri)
+                                t[2 * ((long)cls * 243 + (d * 27 + of) * 3 + cc) + ri] =
+                                    P->alpha_h[2 * (((long)cls * 81 + d * T + oi) * 3 + cc) + ri];
+                }
+    }
+    std::vector<float> t32(t.size());
+    for (size_t i = 0; i < t.size(); ++i) t32[i] = (float)t[i];
+    P->qtab_h = t;
+    SPM_TRY(P->qtab128.ensure(sizeof(double) * t.size()));
+    SPM_TRY(P->qtab64.ensure(sizeof(float) * t32.size()));
+    SPM_CUDA_TRY(cudaMemcpy(P->qtab128.ptr, t.data(), sizeof(double) * t.size(), cudaMemcpyHostToDevice));
+    SPM_CUDA_TRY(cudaMemcpy(P->qtab64.ptr, t32.data(), sizeof(float) * t32.size(), cudaMemcpyHostToDevice));
+    return SPM_OK;
+}
 
 spm_status spm_apply_A_impl(spm_problem_s *P, int prec, const void *x, void *y, int nrhs, cudaStream_t s)
 {
@@ -635,6 +886,8 @@ spm_status apply_A_noalloc_typed(spm_problem_s *P, const void *xv, void *yv, int
         case 128: apply_chunk_v2<R, 128>(xb, yb, m, p, spec, tw, W1, W2, 1, s); break;
         case 256: apply_chunk_v2<R, 256>(xb, yb, m, p, spec, tw, W1, W2, 1, s); break;
         case 512: apply_chunk_v2<R, 512>(xb, yb, m, p, spec, tw, W1, W2, 1, s); break;
+        case 96: apply_chunk_v2<R, 96>(xb, yb, m, p, spec, tw, W1, W2, 1, s); break;
+        case 192: apply_chunk_v2<R, 192>(xb, yb, m, p, spec, tw, W1, W2, 1, s); break;
         default: spm_set_error("unsupported FFT length %d", L); return SPM_ERR_INVALID_ARG;
         }
     }

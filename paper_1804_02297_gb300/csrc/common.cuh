@@ -132,6 +132,8 @@ struct spm_problem_s {
     bool have_stencils = false;
     std::vector<double> alpha_h, beta_h, sv_h; // packed host copies (complex interleaved)
     DevBuf alpha128, alpha64, beta128;
+    DevBuf qtab128, qtab64; // alpha of every class on all 27 offsets (zeros outside tau): [27][3][27][3]
+    std::vector<double> qtab_h; // host copy of the same table (complex interleaved)
     // assembled S (block CSR with 3x3 complex blocks, 27-point pattern)
     bool have_S = false;
     DevBuf S128, S64; // [n^3][27][3][3] complex; absent neighbours hold zeros
@@ -144,6 +146,7 @@ struct spm_problem_s {
 // ------------------------------------------------------------ internal API
 spm_status spm_apply_A_impl(spm_problem_s *P, int prec, const void *x, void *y, int nrhs, cudaStream_t s);
 spm_status spm_apply_Q_impl(spm_problem_s *P, int prec, const void *v, void *y, int nrhs, cudaStream_t s);
+spm_status spm_build_qtable(spm_problem_s *P);
 spm_status spm_build_spectra(spm_problem_s *P);
 spm_status spm_stencils_device(spm_problem_s *P);
 spm_status spm_assemble_S(spm_problem_s *P);

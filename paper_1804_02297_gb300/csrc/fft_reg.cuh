@@ -148,4 +148,196 @@ __device__ __forceinline__ void fft_line(C v[8], int t, Buf buf, Sync sync, cons
     }
 }
 
+
+// K lines at once (E = 8 per thread): the K lines use K shared buffers and
+// share every synchronisation, so K transforms cost the barriers of one.
+// buf(k, pos) addresses line k's buffer.
+template <int DIR, int L, int S, int K, typename C, typename Buf, typename Sync>
+__device__ __forceinline__ void stage_k(C (&v)[K][8], int t, Buf buf, Sync sync, const C *__restrict__ tw)
+{
+    constexpr int T = L / 8;
+    constexpr int r = radix_of(L, S), Ns = span_of(L, S);
+    constexpr int pNs = span_of(L, S - 1);
+    const int kp = t % pNs;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) buf(k, (t - kp) * 8 + kp + q * pNs) = v[k][q];
+    sync();
+    constexpr int nb = 8 / r;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+        for (int u = 0; u < nb; ++u)
+#pragma unroll
+            for (int q = 0; q < r; ++q) v[k][u * r + q] = buf(k, t + u * T + q * (L / r));
+    sync();
+    constexpr int step = L / (r * Ns);
+#pragma unroll
+    for (int u = 0; u < nb; ++u) {
+        const int kk = (t + u * T) % Ns;
+#pragma unroll
+        for (int q = 1; q < r; ++q) {
+            const C w = tw_at<DIR>(tw, q * kk * step);
+#pragma unroll
+            for (int k = 0; k < K; ++k) v[k][u * r + q] = cmul(v[k][u * r + q], w);
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) dft<DIR, r, false>(v[k] + u * r);
+    }
+}
+
+template <int DIR, int L, bool PRUNE, int K, typename C, typename Buf, typename Sync>
+__device__ __forceinline__ void fft_lines(C (&v)[K][8], int t, Buf buf, Sync sync, const C *__restrict__ tw)
+{
+    constexpr int NS = nstages(L);
+#pragma unroll
+    for (int k = 0; k < K; ++k) dft<DIR, 8, PRUNE>(v[k]);
+    if constexpr (NS >= 2) stage_k<DIR, L, 1, K>(v, t, buf, sync, tw);
+    if constexpr (NS >= 3) stage_k<DIR, L, 2, K>(v, t, buf, sync, tw);
+    constexpr int rl = radix_of(L, NS - 1);
+    if constexpr (rl != 8) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            C o[8];
+#pragma unroll
+            for (int u = 0; u < 8 / rl; ++u)
+#pragma unroll
+                for (int q = 0; q < rl; ++q) o[u + (8 / rl) * q] = v[k][u * rl + q];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) v[k][m] = o[m];
+        }
+    }
+}
+
 } // namespace fftr
+
+// ============================================================ 12 per thread
+// L = 96 and 192 (grids n = 48 and 96): E = 12 elements per thread, T = L/12
+// threads per line, stages radix 12 (= 3 x 4), then 4 and 2 (L = 96) or 4 and
+// 4 (L = 192).  Same t + T m register pattern on entry and exit.
+namespace fftr12 {
+
+__host__ __device__ constexpr int radix_of(int L, int s) { return s == 0 ? 12 : (s == 1 ? 4 : (L == 96 ? 2 : 4)); }
+__host__ __device__ constexpr int span_of(int L, int s) { return s == 0 ? 1 : radix_of(L, s - 1) * span_of(L, s - 1); }
+
+// 3-point DFT, w = exp(DIR 2 pi i / 3)
+template <int DIR, typename C> __device__ __forceinline__ void dft3(C &x0, C &x1, C &x2)
+{
+    using R = decltype(x0.x);
+    const R h = (R)0.86602540378443864676; // sqrt(3)/2
+    C t1 = fftr::add(x1, x2), t2 = fftr::sub(x1, x2);
+    C m;
+    m.x = x0.x - (R)0.5 * t1.x;
+    m.y = x0.y - (R)0.5 * t1.y;
+    C s; // DIR i h t2
+    s.x = -(R)DIR * h * t2.y;
+    s.y = (R)DIR * h * t2.x;
+    x0 = fftr::add(x0, t1);
+    x1 = fftr::add(m, s);
+    x2 = fftr::sub(m, s);
+}
+
+// a * exp(DIR 2 pi i M / 12)
+template <int DIR, int M, typename C> __device__ __forceinline__ C w12(C a)
+{
+    using R = decltype(a.x);
+    if constexpr (M == 0) return a;
+    const R cs[7] = {(R)1, (R)0.86602540378443864676, (R)0.5, (R)0, (R)-0.5, (R)-0.86602540378443864676, (R)-1};
+    const R sn7[7] = {(R)0, (R)0.5, (R)0.86602540378443864676, (R)1, (R)0.86602540378443864676, (R)0.5, (R)0};
+    const R c = cs[M], sn = (R)DIR * sn7[M];
+    C r;
+    r.x = a.x * c - a.y * sn;
+    r.y = a.x * sn + a.y * c;
+    return r;
+}
+
+// X[k1 + 3 k2] = sum_n2 w4^(n2 k2) w12^(n2 k1) sum_n1 x[4 n1 + n2] w3^(n1 k1)
+template <int DIR, bool PRUNE, typename C> __device__ __forceinline__ void dft12(C *v)
+{
+    C a[4][3];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+        C x0 = v[n2], x1 = v[n2 + 4], x2 = v[n2 + 8];
+        if (PRUNE) { // x[p] = 0 for p >= 6: x2 = 0 always, x1 = 0 for n2 >= 2
+            x2.x = 0; x2.y = 0;
+            if (n2 >= 2) { x1.x = 0; x1.y = 0; }
+        }
+        dft3<DIR>(x0, x1, x2);
+        a[n2][0] = x0;
+        a[n2][1] = x1;
+        a[n2][2] = x2;
+    }
+    a[1][1] = w12<DIR, 1>(a[1][1]);
+    a[1][2] = w12<DIR, 2>(a[1][2]);
+    a[2][1] = w12<DIR, 2>(a[2][1]);
+    a[2][2] = w12<DIR, 4>(a[2][2]);
+    a[3][1] = w12<DIR, 3>(a[3][1]);
+    a[3][2] = w12<DIR, 6>(a[3][2]);
+#pragma unroll
+    for (int k1 = 0; k1 < 3; ++k1) {
+        C t[4] = {a[0][k1], a[1][k1], a[2][k1], a[3][k1]};
+        fftr::dft4<DIR>(t);
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) v[k1 + 3 * k2] = t[k2];
+    }
+}
+
+template <int DIR, int L, int S, typename C, typename Buf, typename Sync>
+__device__ __forceinline__ void stage(C v[12], int t, Buf buf, Sync sync, const C *__restrict__ tw)
+{
+    constexpr int T = L / 12;
+    constexpr int r = radix_of(L, S), Ns = span_of(L, S);
+    constexpr int pr = radix_of(L, S - 1), pNs = span_of(L, S - 1);
+    constexpr int pnb = 12 / pr, nb = 12 / r;
+#pragma unroll
+    for (int u = 0; u < pnb; ++u) {
+        const int j = t + u * T, k = j % pNs;
+#pragma unroll
+        for (int q = 0; q < pr; ++q) buf((j - k) * pr + k + q * pNs) = v[u * pr + q];
+    }
+    sync();
+#pragma unroll
+    for (int u = 0; u < nb; ++u)
+#pragma unroll
+        for (int q = 0; q < r; ++q) v[u * r + q] = buf(t + u * T + q * (L / r));
+    sync();
+    constexpr int step = L / (r * Ns);
+#pragma unroll
+    for (int u = 0; u < nb; ++u) {
+        const int k = (t + u * T) % Ns;
+#pragma unroll
+        for (int q = 1; q < r; ++q) v[u * r + q] = cmul(v[u * r + q], fftr::tw_at<DIR>(tw, q * k * step));
+        if constexpr (r == 4) fftr::dft4<DIR>(v + u * r);
+        else fftr::dft2<DIR>(v + u * r);
+    }
+}
+
+template <int DIR, int L, bool PRUNE, typename C, typename Buf, typename Sync>
+__device__ __forceinline__ void fft_line(C v[12], int t, Buf buf, Sync sync, const C *__restrict__ tw)
+{
+    dft12<DIR, PRUNE>(v);
+    stage<DIR, L, 1>(v, t, buf, sync, tw);
+    stage<DIR, L, 2>(v, t, buf, sync, tw);
+    constexpr int rl = radix_of(L, 2);
+    C o[12];
+#pragma unroll
+    for (int u = 0; u < 12 / rl; ++u)
+#pragma unroll
+        for (int q = 0; q < rl; ++q) o[u + (12 / rl) * q] = v[u * rl + q];
+#pragma unroll
+    for (int m = 0; m < 12; ++m) v[m] = o[m];
+}
+
+} // namespace fftr12
+
+// elements per thread of the register line FFT for length L
+__host__ __device__ constexpr int line_elems(int L) { return (L == 96 || L == 192) ? 12 : 8; }
+
+// one line, E = line_elems(L) values per thread at positions t + (L/E) m
+template <int DIR, int L, bool PRUNE, typename C, typename Buf, typename Sync>
+__device__ __forceinline__ void line_fft(C *v, int t, Buf buf, Sync sync, const C *__restrict__ tw)
+{
+    if constexpr (line_elems(L) == 12) fftr12::fft_line<DIR, L, PRUNE>(v, t, buf, sync, tw);
+    else fftr::fft_line<DIR, L, PRUNE>(v, t, buf, sync, tw);
+}

@@ -12,7 +12,9 @@
 //   children's Schur complements are extend-added,
 //   F11 = P L U (partial pivoting inside the own block),
 //   X = F11^{-1} F12,   update = F22 - F21 X  -> parent.
-// Each node keeps G = [F11^{-1}; F21 F11^{-1}] (front x own) and X = F11^{-1} F12.
+// Each node keeps G = [F11^{-1}; F21 F11^{-1}] (front x own) and X = F11^{-1} F12,
+// in the factor's precision or (SPM_C64H) as binary16 pairs scaled per column by
+// the column's largest component, which halves the bytes every solve reads.
 // Solve, one batched pass per tree level:
 //   forward (deepest level first): [y; t] = G w_own, w_own = y, w_bnd -= t
 //   backward (root first):         w_own -= X w_bnd.
@@ -23,9 +25,11 @@
 // kernels here.
 #include <cublas_v2.h>
 #include <cuComplex.h>
+#include <cuda_fp16.h>
 #include <cusolverDn.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -43,6 +47,7 @@ struct Node {
     long rel_off = 0;        // offset of the child-bnd -> parent-front map (unknowns)
     long fac_off = 0;        // persistent factor storage (elements)
     long piv_off = 0;        // pivots
+    long scale_off = 0;      // per-column scales of G then X (half storage)
     int depth = 0;
 };
 
@@ -153,7 +158,7 @@ template <typename C> __global__ void k_identity(C *a, int n, int ld)
 // output block (rows x nrhs) at out_unit * nrhs, in_unit / out_unit being prefix
 // sums of cols / rows over the level.
 struct LevelNode {
-    long mat_off, in_unit, out_unit;
+    long mat_off, in_unit, out_unit, scale_off;
     int rows, cols;
     int own_pts, bnd_pts; // offsets into the point list
     int nown, nbnd;
@@ -161,11 +166,18 @@ struct LevelNode {
 struct Tile {
     int node, row0, col0;
 };
-constexpr int GT_ROWS = 256, GT_COLS = 256, GT_NB = 4;
+constexpr int GT_ROWS = 256, GT_COLS = 256;
 
-// out[node] += M[node][row0:+256, col0:+256] * in[node][col0:+256, :]
-template <typename C>
-__global__ void __launch_bounds__(GT_ROWS) k_level_gemv(const C *__restrict__ M, const LevelNode *__restrict__ nodes,
+// out[node] += M[node][row0:+256, col0:+256] * in[node][col0:+256, :]; GT_NB
+// right-hand sides per pass over the tile (1 for a single RHS, 4 for blocks).
+// S = C: stored as is; S = __half2: binary16 pairs, column c scaled by scale[c].
+__device__ __forceinline__ float2 load_as(const float2 *p) { return *p; }
+__device__ __forceinline__ double2 load_as(const double2 *p) { return *p; }
+__device__ __forceinline__ float2 load_as(const __half2 *p) { return __half22float2(*p); }
+
+template <typename C, int GT_NB, typename S>
+__global__ void __launch_bounds__(GT_ROWS) k_level_gemv(const S *__restrict__ M, const float *__restrict__ scales,
+                                                        const LevelNode *__restrict__ nodes,
                                                         const Tile *__restrict__ tiles, const C *__restrict__ in,
                                                         C *out, int nrhs)
 {
@@ -177,6 +189,7 @@ __global__ void __launch_bounds__(GT_ROWS) k_level_gemv(const C *__restrict__ M,
     const int ncol = min(GT_COLS, nd.cols - tl.col0);
     const C *inb = in + nd.in_unit * nrhs;
     C *outb = out + nd.out_unit * nrhs;
+    constexpr bool SCALED = !std::is_same<S, C>::value;
     for (int b0 = 0; b0 < nrhs; b0 += GT_NB) {
         const int nb = min(GT_NB, nrhs - b0);
         __syncthreads();
@@ -185,7 +198,14 @@ __global__ void __launch_bounds__(GT_ROWS) k_level_gemv(const C *__restrict__ M,
             C v;
             v.x = 0;
             v.y = 0;
-            if (c < ncol && b < nb) v = inb[(long)(b0 + b) * nd.cols + tl.col0 + c];
+            if (c < ncol && b < nb) {
+                v = inb[(long)(b0 + b) * nd.cols + tl.col0 + c];
+                if constexpr (SCALED) {
+                    const R sc = (R)scales[nd.scale_off + tl.col0 + c];
+                    v.x *= sc;
+                    v.y *= sc;
+                }
+            }
             xs[i] = v;
         }
         __syncthreads();
@@ -193,10 +213,11 @@ __global__ void __launch_bounds__(GT_ROWS) k_level_gemv(const C *__restrict__ M,
             R ax[GT_NB], ay[GT_NB];
 #pragma unroll
             for (int b = 0; b < GT_NB; ++b) { ax[b] = 0; ay[b] = 0; }
-            const C *col = M + nd.mat_off + (long)tl.col0 * nd.rows + r;
-#pragma unroll 4
+            const S *col = M + nd.mat_off + (long)tl.col0 * nd.rows + r;
+            constexpr int UNR = SCALED ? 16 : 4; // 4-byte elements: more loads in flight
+#pragma unroll UNR
             for (int c = 0; c < ncol; ++c) {
-                C g = col[(long)c * nd.rows];
+                const C g = load_as(col + (long)c * nd.rows);
 #pragma unroll
                 for (int b = 0; b < GT_NB; ++b) {
                     C xv = xs[b * GT_COLS + c];
@@ -211,6 +232,37 @@ __global__ void __launch_bounds__(GT_ROWS) k_level_gemv(const C *__restrict__ M,
             }
         }
     }
+}
+
+// scale[c] = largest |component| of column c of an (m x ncol, ld m) block (1 if zero)
+__global__ void k_col_scales(const float2 *__restrict__ a, int m, int ncol, float *scale)
+{
+    const int c = blockIdx.x;
+    float mx = 0.f;
+    for (int r = threadIdx.x; r < m; r += blockDim.x) {
+        float2 v = a[(long)c * m + r];
+        mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+    }
+    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_down_sync(0xffffffffu, mx, off));
+    __shared__ float red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmaxf(t, red[w]);
+        scale[c] = t > 0.f ? t : 1.f;
+    }
+}
+
+// dst = src / scale[column] as binary16 pairs
+__global__ void k_to_half(__half2 *dst, const float2 *__restrict__ src, int m, int ncol,
+                          const float *__restrict__ scale)
+{
+    long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (long)m * ncol) return;
+    const float inv = 1.f / scale[gid / m];
+    const float2 v = src[gid];
+    dst[gid] = __floats2half2_rn(v.x * inv, v.y * inv);
 }
 
 // node whose element range [unit[i] * nrhs, unit[i+1] * nrhs) holds gid
@@ -279,6 +331,8 @@ __global__ void k_level_scatter(C *w, const C *__restrict__ packed, const LevelN
 
 struct NDFactor {
     int prec = 0;
+    bool half_store = false; // blocks as scaled binary16 pairs (complex64 factor only)
+    DevBuf scales;           // per-column scales (half storage)
     int n = 0;
     std::vector<Node> nodes; // post-order
     DevBuf pts, maps, rels;  // int lists
@@ -307,7 +361,7 @@ struct NDFactor {
         if (cusolver) cusolverDnDestroy(cusolver);
         pts.release(); maps.release(); rels.release(); fac.release(); piv.release();
         front.release(); stack.release(); work.release(); info.release(); solve_ws.release();
-        lv_nodes.release(); lv_units.release(); lv_tiles.release();
+        lv_nodes.release(); lv_units.release(); lv_tiles.release(); scales.release();
     }
 };
 
@@ -341,7 +395,7 @@ int build_tree(std::vector<Node> &nodes, const int lo[3], const int hi[3], int d
 } // namespace
 
 template <typename R>
-static spm_status factor_typed(spm_problem_s *P, NDFactor *F)
+static spm_status factor_typed(spm_problem_s *P, NDFactor *F, bool half_store)
 {
     using BT = blas_t<R>;
     using C = typename BT::C;
@@ -407,7 +461,8 @@ static spm_status factor_typed(spm_problem_s *P, NDFactor *F)
         }
     }
     // storage
-    long fac_total = 0, piv_total = 0;
+    F->half_store = half_store;
+    long fac_total = 0, piv_total = 0, scale_total = 0, max_gx = 0;
     size_t max_f = 0, max_upd_stack = 0, stack_now = 0;
     std::vector<size_t> upd_size(NN, 0);
     for (int id = 0; id < NN; ++id) {
@@ -417,6 +472,9 @@ static spm_status factor_typed(spm_problem_s *P, NDFactor *F)
         fac_total += f * o3 + o3 * b3;
         nd.piv_off = piv_total;
         piv_total += o3;
+        nd.scale_off = scale_total;
+        scale_total += f;
+        max_gx = std::max(max_gx, f * o3 + o3 * b3);
         max_f = std::max(max_f, (size_t)f);
         F->max_own3 = std::max(F->max_own3, (size_t)o3);
         F->max_bnd3 = std::max(F->max_bnd3, (size_t)b3);
@@ -434,7 +492,12 @@ static spm_status factor_typed(spm_problem_s *P, NDFactor *F)
     SPM_CUDA_TRY(cudaMemcpy(F->maps.ptr, maps.data(), sizeof(int) * maps.size(), cudaMemcpyHostToDevice));
     if (!rels.empty())
         SPM_CUDA_TRY(cudaMemcpy(F->rels.ptr, rels.data(), sizeof(int) * rels.size(), cudaMemcpyHostToDevice));
-    SPM_TRY(F->fac.ensure(sizeof(C) * fac_total));
+    SPM_TRY(F->fac.ensure((half_store ? sizeof(__half2) : sizeof(C)) * fac_total));
+    DevBuf gx; // complex64 staging of G and X before conversion (half storage)
+    if (half_store) {
+        SPM_TRY(gx.ensure(sizeof(C) * max_gx));
+        SPM_TRY(F->scales.ensure(sizeof(float) * scale_total));
+    }
     SPM_TRY(F->piv.ensure(sizeof(int) * std::max<long>(piv_total, 1)));
     SPM_TRY(F->front.ensure(sizeof(C) * max_f * max_f));
     SPM_TRY(F->stack.ensure(sizeof(C) * std::max<size_t>(max_upd_stack, 1)));
@@ -498,7 +561,7 @@ static spm_status factor_typed(spm_problem_s *P, NDFactor *F)
             top += upd_size[id];
         }
         // persistent: G = [F11^{-1}; F21 F11^{-1}] (f x o3, ld f) then X (o3 x b3, ld o3)
-        C *G = fac + nd.fac_off;
+        C *G = half_store ? gx.as<C>() : fac + nd.fac_off;
         k_identity<C><<<blocks((long)o3 * o3), 256, 0, s>>>(G, o3, f);
         if (BT::getrs(F->cusolver, o3, o3, front, f, dpiv + nd.piv_off, G, f, dinfo + 1) != CUSOLVER_STATUS_SUCCESS) {
             spm_set_error("getrs (inverse) failed at node %d", id);
@@ -512,6 +575,19 @@ static spm_status factor_typed(spm_problem_s *P, NDFactor *F)
             }
             k_copy_block<C><<<blocks((long)o3 * b3), 256, 0, s>>>(G + (long)f * o3, o3, front + (long)o3 * f, f, o3,
                                                                   b3);
+        }
+        if constexpr (sizeof(R) == 4) {
+            if (half_store) {
+                float *sc = F->scales.as<float>() + nd.scale_off;
+                __half2 *h = F->fac.as<__half2>() + nd.fac_off;
+                const float2 *g2 = reinterpret_cast<const float2 *>(G);
+                k_col_scales<<<o3, 256, 0, s>>>(g2, f, o3, sc);
+                k_to_half<<<blocks((long)f * o3), 256, 0, s>>>(h, g2, f, o3, sc);
+                if (b3 > 0) {
+                    k_col_scales<<<b3, 256, 0, s>>>(g2 + (long)f * o3, o3, b3, sc + o3);
+                    k_to_half<<<blocks((long)o3 * b3), 256, 0, s>>>(h + (long)f * o3, g2 + (long)f * o3, o3, b3, sc + o3);
+                }
+            }
         }
         SPM_CUDA_TRY(cudaGetLastError());
     }
@@ -548,6 +624,7 @@ static spm_status factor_typed(spm_problem_s *P, NDFactor *F)
                 L.cols = fwd ? o3 : b3;
                 if (L.cols == 0) continue;
                 L.mat_off = fwd ? nd.fac_off : nd.fac_off + (long)f * o3;
+                L.scale_off = fwd ? nd.scale_off : nd.scale_off + o3;
                 L.in_unit = ui.back();
                 L.out_unit = uo.back();
                 L.own_pts = (int)nd.own_off;
@@ -609,7 +686,20 @@ static spm_status solve_typed(spm_problem_s *P, NDFactor *F, const void *bv, voi
     C *out = in + pin;
     const int *dpts = F->pts.as<int>();
     const C *fac = F->fac.as<C>();
+    const __half2 *fac16 = F->fac.as<__half2>();
+    const float *scales = F->scales.as<float>();
     const LevelNode *tn = F->lv_nodes.as<LevelNode>();
+    auto gemv = [&](int ntiles, const LevelNode *nodes, const Tile *tiles) {
+        if constexpr (sizeof(R) == 4) {
+            if (F->half_store) {
+                if (nrhs == 1) k_level_gemv<C, 1, __half2><<<ntiles, GT_ROWS, 0, s>>>(fac16, scales, nodes, tiles, in, out, nrhs);
+                else k_level_gemv<C, 4, __half2><<<ntiles, GT_ROWS, 0, s>>>(fac16, scales, nodes, tiles, in, out, nrhs);
+                return;
+            }
+        }
+        if (nrhs == 1) k_level_gemv<C, 1, C><<<ntiles, GT_ROWS, 0, s>>>(fac, scales, nodes, tiles, in, out, nrhs);
+        else k_level_gemv<C, 4, C><<<ntiles, GT_ROWS, 0, s>>>(fac, scales, nodes, tiles, in, out, nrhs);
+    };
     const long *tu = F->lv_units.as<long>();
     const Tile *tt = F->lv_tiles.as<Tile>();
     const int NL = (int)F->levels.size();
@@ -619,7 +709,7 @@ static spm_status solve_typed(spm_problem_s *P, NDFactor *F, const void *bv, voi
         k_level_gather<C><<<blocks(lv.pack_f_in * nrhs), 256, 0, s>>>(in, x, tn + lv.nodes_f, tu + lv.units_f_in, dpts,
                                                                        lv.nn_f, n3, nrhs, 0);
         SPM_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(C) * lv.pack_f_out * nrhs, s));
-        k_level_gemv<C><<<lv.ntiles_f, GT_ROWS, 0, s>>>(fac, tn + lv.nodes_f, tt + lv.tiles_f, in, out, nrhs);
+        gemv(lv.ntiles_f, tn + lv.nodes_f, tt + lv.tiles_f);
         k_level_scatter<C><<<blocks(lv.pack_f_out * nrhs), 256, 0, s>>>(x, out, tn + lv.nodes_f, tu + lv.units_f_out,
                                                                          dpts, lv.nn_f, n3, nrhs, 0);
     }
@@ -629,7 +719,7 @@ static spm_status solve_typed(spm_problem_s *P, NDFactor *F, const void *bv, voi
         k_level_gather<C><<<blocks(lv.pack_b_in * nrhs), 256, 0, s>>>(in, x, tn + lv.nodes_b, tu + lv.units_b_in, dpts,
                                                                        lv.nn_b, n3, nrhs, 1);
         SPM_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(C) * lv.pack_b_out * nrhs, s));
-        k_level_gemv<C><<<lv.ntiles_b, GT_ROWS, 0, s>>>(fac, tn + lv.nodes_b, tt + lv.tiles_b, in, out, nrhs);
+        gemv(lv.ntiles_b, tn + lv.nodes_b, tt + lv.tiles_b);
         k_level_scatter<C><<<blocks(lv.pack_b_out * nrhs), 256, 0, s>>>(x, out, tn + lv.nodes_b, tu + lv.units_b_out,
                                                                          dpts, lv.nn_b, n3, nrhs, 1);
     }
@@ -643,8 +733,9 @@ spm_status spm_factor_impl(spm_problem_s *P, int prec)
     spm_factor_free(slot);
     slot = nullptr;
     NDFactor *F = new NDFactor();
-    F->prec = prec;
-    spm_status st = prec == SPM_C128 ? factor_typed<double>(P, F) : factor_typed<float>(P, F);
+    F->prec = prec == SPM_C128 ? SPM_C128 : SPM_C64;
+    spm_status st = prec == SPM_C128 ? factor_typed<double>(P, F, false)
+                                     : factor_typed<float>(P, F, prec == SPM_C64H);
     if (st != SPM_OK) {
         delete F;
         return st;

@@ -503,5 +503,5 @@ spm_status spm_stencils_device(spm_problem_s *P)
     SPM_CUDA_TRY(cudaMemcpy(P->alpha64.ptr, a32.data(), sizeof(float) * a32.size(), cudaMemcpyHostToDevice));
     SPM_CUDA_TRY(cudaMemcpy(P->beta128.ptr, beta_all.ptr, beta_all.bytes, cudaMemcpyDeviceToDevice));
     P->have_stencils = true;
-    return SPM_OK;
+    return spm_build_qtable(P);
 }

@@ -236,6 +236,26 @@ def workload(name: str):
         k = wavenumber_for_grid(n)
         eps, grad = medium_bumps(n, seed=5, count=32)
         einc = plane_wave_block(n, k, 8)
+    elif name == "n256_bumps32":
+        n = 256
+        k = wavenumber_for_grid(n)
+        eps, grad = medium_bumps(n, seed=6, count=32)
+        einc = plane_wave(n, k, (0, 0, 1), (1, 0, 0))[None]
     else:
         raise KeyError(name)
     return dict(n=n, omega=k, eps=eps, grad=grad, einc=einc)
+
+
+def uneven_batch(count: int = 32, sizes=(32, 48, 64, 96), base_seed: int = 100):
+    """``count`` independent problems: problem q draws n from ``sizes`` (splitmix64,
+    seed base_seed + q), k = pi n/4, its own 8-bump medium (same seed) and one
+    plane wave along +z polarised along x."""
+    out = []
+    for q in range(count):
+        rng = SplitMix64(base_seed + q)
+        n = sizes[min(int(rng.uniform() * len(sizes)), len(sizes) - 1)]
+        k = wavenumber_for_grid(n)
+        eps, grad = medium_bumps(n, seed=base_seed + q, count=8)
+        einc = plane_wave(n, k, (0, 0, 1), (1, 0, 0))
+        out.append(dict(n=n, omega=k, eps=eps, grad=grad, einc=einc))
+    return out

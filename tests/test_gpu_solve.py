@@ -182,3 +182,35 @@ def test_batched_apply_equals_single(spm):
         P.apply_A(X[b].contiguous(), yb)
         torch.cuda.synchronize()
         assert torch.equal(yb, Y[b])
+
+
+def test_half_storage_factor(spm):
+    """SPM_C64H keeps the complex64 factor's blocks as column-scaled binary16:
+    S^-1 is then accurate to about 1e-3 (11-bit significands), and the solve
+    still reaches the FP64 true residual because the outer loop is FP64."""
+    n = 16
+    k = si.wavenumber_for_grid(n)
+    eps, grad = si.medium_bumps(n, seed=3, count=8)
+    P = spm.Problem(n, k, eps, grad)
+    P.build_stencils(spm.SPM_C64H)
+    b = si.random_field(n, 17)
+    x = torch.zeros(b.shape, dtype=torch.complex64, device="cuda")
+    P.solve_S(dev(b, torch.complex64), x)
+    y = torch.zeros(b.shape, dtype=torch.complex128, device="cuda")
+    P.apply_S(x.to(torch.complex128), y)
+    torch.cuda.synchronize()
+    r = rel(y.cpu().numpy(), b)
+    print(f"half-storage factor: S residual {r:.2e}")
+    assert r < 2e-2
+    wl = si.workload("n64_bumps8")
+    n = wl["n"]
+    P = spm.Problem(n, wl["omega"], wl["eps"], wl["grad"])
+    P.build_stencils(spm.SPM_C64H)
+    e = dev(wl["einc"])
+    g = torch.zeros_like(e)
+    P.rhs_from_incident(e, g)
+    x = torch.zeros_like(g)
+    info, _ = P.solve(g, x, prec=spm.SPM_MIXED, tol=1e-6, maxit=200)
+    print(f"n=64 mixed, half-storage factor: iterations {info.iterations}, relres {info.true_relres:.2e}")
+    assert info.true_relres <= 1e-6
+    assert info.iterations <= 16
