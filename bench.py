@@ -74,6 +74,24 @@ def compulsory_bytes(n, prec, nrhs=1):
     return el * (nrhs * 3 * N + N + 3 * N + 4 * (n + 1) ** 3 + nrhs * 3 * N)
 
 
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
+FP64_PEAK_TFLOPS = 1.25  # GB300 FP64 rate (tensor and CUDA cores), nominal
+
+
+def algorithmic_flops(n, op, nrhs=1):
+    """Flops of one apply by the usual count: 7 zero-padded 3-D FFTs of L^3
+    points at 5 L^3 log2(L^3) each, times 7/12 for the pruned zero half and the
+    cropped outputs, 48 L^3 for the Fourier-side product (6 complex MACs per
+    frequency), and 1944 n^3 for Q (243 complex MACs per point)."""
+    import math
+    L = 2 * n
+    L3 = float(L) ** 3
+    f = 7 * 5 * L3 * math.log2(L3) * 7.0 / 12.0 + 48 * L3
+    if op == "QA":
+        f += 1944.0 * n ** 3
+    return f * nrhs
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -208,21 +226,28 @@ def aggregate_timing(total_ms, steps, units_per_step, world, dist=None, device="
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("apply.cu", "fft.cuh", "common.cuh"):
+    for f in ("apply.cu", "fft_reg.cuh", "common.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1804_02297_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def recorded_traffic(workload, prec, op):
-    """DRAM bytes per apply from the committed ncu summary, if the kernels are unchanged."""
-    path = os.path.join(ROOT, "profiles", "apply_traffic.json")
+    """DRAM bytes per apply (read + write, all launches of one apply) from the
+    committed ncu summary profiles/apply_dram_traffic.md, or None when the
+    kernel sources changed since the counters were taken (hash mismatch)."""
+    path = os.path.join(ROOT, "profiles", "apply_dram_traffic.md")
     if not os.path.exists(path):
         return None
-    d = json.load(open(path))
-    e = d.get(f"{workload}/{prec}/{op}")
-    if not e or e.get("source_hash") != kernel_source_hash():
-        return None
-    return e.get("dram_bytes_per_apply")
+    want = f"{workload}/{prec}/{op}"
+    for line in open(path):
+        f = line.strip().strip("|").split("|")
+        f = [x.strip().strip("`") for x in f]
+        if len(f) >= 3 and f[0] == want and f[2] == kernel_source_hash():
+            try:
+                return int(f[1])
+            except ValueError:
+                return None
+    return None
 
 
 def chunk_of(P, n, prec):
@@ -269,36 +294,47 @@ def run_uneven(args, torch, spm, rank, world, local):
     alg = sum(compulsory_bytes(q["n"], args.prec) for q in probs)
     peak, peak_kind = peaks()
     achieved = alg / (ms_per_step / 1000.0) / 1e9
+    flops = sum(algorithmic_flops(q["n"], "A") for q in probs)
+    fpeak = FP32_PEAK_TFLOPS if args.prec == "c64" else FP64_PEAK_TFLOPS
+    tflops = flops / (ms_per_step / 1000.0) / 1e12
     line = {"metric": METRIC, "value": value, "unit": "problem applies/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
             "config": {"workload": "uneven32", "sizes": sorted(set(q["n"] for q in probs)), "problems": len(probs),
                        "op": "A", "graph": "one CUDA graph launch per step", "l2": "flushed between steps",
                        "parallelism": f"replicas{world}"},
-            "roofline": {"bound": "hbm", "kernel": "batched apply_A (graph)", "achieved": achieved, "peak": peak,
-                         "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
-                         "algorithmic_bytes": alg, "traffic": None},
+            "roofline": {"bound": "alu", "kernel": "batched apply_A (graph)", "achieved": tflops, "peak": fpeak,
+                         "unit": "TFLOP/s", "frac": tflops / fpeak, "algorithmic_flops": flops, "traffic": None,
+                         "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                                 "peak_source": peak_kind, "algorithmic_bytes": alg}},
             "gpu_launches": 5 * len(probs) * args.steps, "clocks": clocks}
     if args.solve != "none":
+        # solves: the problems with n <= 64 (the nested-dissection factor of one
+        # n = 96 problem alone needs 65-131 GB, so six of them cannot stay resident)
+        sub = [q for q in probs if q["n"] <= 64]
+        B2 = spm.Batch([q["n"] for q in sub], [q["omega"] for q in sub], [q["eps"] for q in sub],
+                       [q["grad"] for q in sub])
         t0 = time.perf_counter()
-        B.build_stencils(spm.SPM_C64)
+        B2.build_stencils(spm.SPM_C64H)
         torch.cuda.synchronize()
         setup_s = time.perf_counter() - t0
         gs = []
-        for i, q in enumerate(probs):
+        for i, q in enumerate(sub):
             e = torch.from_numpy(q["einc"]).to("cuda")
             g = torch.zeros_like(e)
-            B.problems[i].rhs_from_incident(e, g)
+            B2.problems[i].rhs_from_incident(e, g)
             gs.append(g)
         xs2 = [torch.zeros_like(g) for g in gs]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        infos, st = B.solve(gs, xs2, prec=spm.SPM_MIXED, tol=1e-6, maxit=400, check=False)
+        infos, st = B2.solve(gs, xs2, prec=spm.SPM_MIXED, tol=1e-6, maxit=400, check=False)
         torch.cuda.synchronize()
-        line["solve"] = {"mixed_batch_time_s": time.perf_counter() - t0, "status": st,
+        line["solve"] = {"problems": len(sub), "sizes": sorted(set(q["n"] for q in sub)),
+                         "mixed_half_factor_batch_time_s": time.perf_counter() - t0, "status": st,
                          "max_iterations": max(i.iterations for i in infos),
                          "max_true_relres": max(i.true_relres for i in infos),
-                         "setup_stencils_factor_c64_s": setup_s}
+                         "setup_stencils_factor_c64_half_storage_s": setup_s,
+                         "excluded": "n = 96 problems: apply only (factor memory)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -445,11 +481,23 @@ def run_ours(args):
     peak, peak_kind = peaks()
     alg = compulsory_bytes(n, args.prec, nrhs)
     achieved = alg / (ms_per_step / 1000.0) / 1e9
-    roof = {"bound": "hbm", "kernel": f"apply_{args.op} ({launches_per_step} launches)",
-            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "peak_source": peak_kind, "algorithmic_bytes": alg,
-            "traffic": recorded_traffic(args.workload, args.prec, args.op)}
-
+    flops = algorithmic_flops(n, args.op, nrhs)
+    tflops = flops / (ms_per_step / 1000.0) / 1e12
+    fpeak = FP32_PEAK_TFLOPS if args.prec == "c64" else FP64_PEAK_TFLOPS
+    # roofline: the bound whose minimum time is longer (flops at the ALU peak vs
+    # compulsory bytes at the measured HBM bandwidth) is the one reported
+    alu_bound = flops / (fpeak * 1e12) > alg / (peak * 1e9)
+    hbm = {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
+           "algorithmic_bytes": alg, "traffic": recorded_traffic(args.workload, args.prec, args.op)}
+    alu = {"achieved": tflops, "peak": fpeak, "unit": "TFLOP/s", "frac": tflops / fpeak,
+           "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if args.prec == "c64"
+           else "nominal GB300 FP64", "algorithmic_flops": flops}
+    roof = dict(alu if alu_bound else hbm)
+    roof["bound"] = "alu" if alu_bound else "hbm"
+    roof["kernel"] = f"apply_{args.op} ({launches_per_step} launches)"
+    roof["traffic"] = hbm["traffic"]
+    roof["hbm"] = hbm
+    roof["alu"] = alu
     line = {"metric": METRIC, "value": value, "unit": "field applies/s" if nrhs > 1 else "applies/s",
             "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",

@@ -183,3 +183,21 @@ def test_plane_wave_and_rhs(spm):
     torch.cuda.synchronize()
     gref = ref - oracle.apply_fft(n, k, m, p, ref)
     assert rel(g.cpu().numpy(), gref) < 1e-12
+
+
+def test_apply_A_full_size_n128_c64(spm):
+    """n = 128 grid of the 8-RHS workload (32 seeded bumps, k = 32 pi), complex64,
+    one field against the oracle (complex64 tolerance on (A - I) x)."""
+    wl = si.workload("n128_bumps32_rhs8")
+    n, k = wl["n"], wl["omega"]
+    P = spm.Problem(n, k, wl["eps"], wl["grad"])
+    m, p = oracle.medium(wl["eps"], wl["grad"])
+    x = wl["einc"][3]
+    ref = oracle.apply_fft(n, k, m, p, x)
+    y = torch.zeros(x.shape, dtype=torch.complex64, device="cuda")
+    P.apply_A(to_dev(x, torch.complex64), y)
+    torch.cuda.synchronize()
+    got = y.cpu().numpy().astype(np.complex128)
+    e = rel(got - x, ref - x)
+    print(f"n=128 c64: rel err of (A-I)x = {e:.2e}")
+    assert e < 2e-5
