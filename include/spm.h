@@ -10,7 +10,8 @@
  *   i = (i1,i2,i3), 1 <= i_d <= n, at x = i*h.  Grid arrays are [i3][i2][i1]
  *   with i1 fastest.
  * Fields: a vector field is [d][i3][i2][i1], d = 0,1,2 (the paper's E^1,E^2,E^3);
- *   nrhs fields are stacked outermost: [b][d][i3][i2][i1].  Complex numbers are
+ *   nrhs fields are stacked outermost: [b][d][i3][i2][i1], 0 <= nrhs <= 65535
+ *   (SPM_ERR_INVALID_ARG otherwise).  Complex numbers are
  *   interleaved (re, im).  SPM_C128 buffers hold double pairs, SPM_C64 buffers
  *   float pairs.
  * Memory: arguments named *_host are host pointers, *_dev device pointers.  The
@@ -150,8 +151,36 @@ spm_status spm_set_stencils(spm_problem prob, const double *alpha_host, const do
 spm_status spm_get_stencils(spm_problem prob, double *alpha_host, double *beta_host, double *sv_host);
 
 /* Factor the assembled S (nested dissection, multifrontal LU on the device) in
- * `prec` (SPM_C128 or SPM_C64).  Synchronises. */
+ * `prec` (SPM_C128, SPM_C64 or SPM_C64H).  Pivoting stays inside each front, so
+ * a box of the dissection whose part of S is nearly singular spoils the factor
+ * even when S itself is well conditioned.  Two safeguards: pivots of a front
+ * below 1e-8 (SPM_C128) or 1e-4 (complex64) times the front's largest pivot are
+ * raised to that size (the factor is then exact for S plus a perturbation of
+ * that rank); and the factor is probed:
+ * x = S^{-1} b for a fixed pseudo-random b, and the residual ||S x - b|| / ||b||
+ * (S x in complex128) must be at most 1e-6 (SPM_C128), 3e-2 (SPM_C64) or 0.3
+ * (SPM_C64H); otherwise up to three other trees (cut planes moved by one) are
+ * factored and the most accurate factor is kept.  Synchronises. */
 spm_status spm_factor_S(spm_problem prob, spm_prec prec);
+
+/* Factor S on one tree variant (0 = cuts through the middle planes; 1, 2, 3 =
+ * every cut moved one plane down, up, or alternately by depth), without the
+ * retry; the probe residual is still recorded for spm_factor_info.
+ * SPM_ERR_INVALID_ARG for a variant outside [0, 4). */
+spm_status spm_factor_S_tree(spm_problem prob, spm_prec prec, int variant);
+
+/* Report on the current factor in `prec` (SPM_C128, or SPM_C64 / SPM_C64H for
+ * the complex64 slot): tree variant kept (0 = middle cuts), factorisations run
+ * by the last spm_factor_S, whether blocks are in half storage, the number of
+ * raised pivots, and the probe residual described above.  SPM_ERR_NOT_BUILT if there is no such factor. */
+typedef struct {
+    int variant;
+    int attempts;
+    int half_store;
+    int raised_pivots;      /* pivots raised by the static perturbation in the kept factor */
+    double probe_relres;
+} spm_factor_report;
+spm_status spm_factor_info(spm_problem prob, spm_prec prec, spm_factor_report *out);
 
 /* y = S x for nrhs fields (sparse product with the assembled S). */
 spm_status spm_apply_S(spm_problem prob, spm_prec prec, const void *x_dev, void *y_dev,
@@ -161,6 +190,25 @@ spm_status spm_apply_S(spm_problem prob, spm_prec prec, const void *x_dev, void 
  * substitution through the elimination tree). */
 spm_status spm_solve_S(spm_problem prob, spm_prec prec, const void *b_dev, void *x_dev,
                        int nrhs, void *stream);
+
+/* Apply plan (process-wide, per FFT length L = 2n or the radix-3 lengths 96
+ * and 192, and per apply precision SPM_C128 / SPM_C64): the z-pass kernel.
+ *   0  four lines per thread block with all fields in registers (lengths other
+ *      than 96 and 192),
+ *   1  one field at a time after a cp.async prefetch of all four (L >= 32, 96, 192),
+ *   2  persistent, fed by TMA bulk-tensor copies into two shared-memory stages
+ *      (L >= 32),
+ *  -1  not chosen yet: the next apply of that length times the candidates on
+ *      its own data (outside stream capture) and keeps the fastest.
+ * SPM_ERR_INVALID_ARG for an unknown length or a variant the length lacks. */
+spm_status spm_get_apply_plan(spm_prec prec, int L, int *zvariant);
+spm_status spm_set_apply_plan(spm_prec prec, int L, int zvariant);
+
+/* Synchronise the device and report whether any kernel of this problem gave up
+ * a bounded wait since the last call (SPM_ERR_TIMEOUT, then cleared): the
+ * TMA-fed z-pass waits on its copies with an iteration limit instead of
+ * spinning forever, and leaves its output incomplete when the limit is hit. */
+spm_status spm_device_status(spm_problem prob);
 
 /* ------------------------------------------------------------- solving */
 

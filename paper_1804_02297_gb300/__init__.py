@@ -23,7 +23,7 @@ SPM_C128, SPM_C64, SPM_MIXED, SPM_C64H = 0, 1, 2, 3
 # every symbol include/spm.h declares
 EXPORTS = [
     "spm_create_problem", "spm_destroy", "spm_problem_info", "spm_apply_A", "spm_apply_QA", "spm_apply_Q",
-    "spm_build_stencils", "spm_set_stencils", "spm_get_stencils", "spm_factor_S", "spm_apply_S",
+    "spm_build_stencils", "spm_set_stencils", "spm_get_stencils", "spm_factor_S", "spm_factor_S_tree", "spm_factor_info", "spm_device_status", "spm_get_apply_plan", "spm_set_apply_plan", "spm_apply_S",
     "spm_solve_S", "spm_incident_plane_wave", "spm_rhs_from_incident", "spm_solve", "spm_kernel_entries",
     "spm_lattice_constant", "spm_last_error", "spm_apply_A_noalloc",
     "spm_create_batch", "spm_destroy_batch", "spm_batch_size", "spm_batch_problem", "spm_batch_build_stencils",
@@ -31,10 +31,30 @@ EXPORTS = [
 ]
 
 
+ZPASS_FOUR, ZPASS_ONE, ZPASS_TMA = 0, 1, 2
+
+
+def get_apply_plan(prec, L):
+    """z-pass kernel chosen for FFT length L in ``prec`` (-1: not chosen yet)."""
+    z = ctypes.c_int()
+    _check(lib.spm_get_apply_plan(prec, L, ctypes.byref(z)))
+    return z.value
+
+
+def set_apply_plan(prec, L, zvariant):
+    """Fix the z-pass kernel for FFT length L in ``prec`` (-1: time the candidates again)."""
+    _check(lib.spm_set_apply_plan(prec, L, zvariant))
+
+
 class SpmError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"libspm status {status}: {msg}")
         self.status = status
+
+
+class FactorReport(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int), ("attempts", ctypes.c_int), ("half_store", ctypes.c_int),
+                ("raised_pivots", ctypes.c_int), ("probe_relres", ctypes.c_double)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -59,6 +79,11 @@ def _load():
         "spm_set_stencils": [P, P, P],
         "spm_get_stencils": [P, P, P, P],
         "spm_factor_S": [P, I],
+        "spm_factor_info": [P, I, ctypes.POINTER(FactorReport)],
+        "spm_factor_S_tree": [P, I, I],
+        "spm_device_status": [P],
+        "spm_get_apply_plan": [I, I, ctypes.POINTER(I)],
+        "spm_set_apply_plan": [I, I, I],
         "spm_apply_S": [P, I, P, P, I, P],
         "spm_solve_S": [P, I, P, P, I, P],
         "spm_incident_plane_wave": [P, I, P, P, I, P, P],
@@ -166,6 +191,10 @@ class Problem:
         _check(lib.spm_problem_info(self.h, ctypes.byref(n), ctypes.byref(k), ctypes.byref(u)))
         return n.value, k.value, u.value
 
+    def device_status(self):
+        """Synchronise; raise SpmError(SPM_ERR_TIMEOUT) if a bounded device wait gave up."""
+        _check(lib.spm_device_status(self.h))
+
     # ---- operator
     def apply_A(self, x, y, stream=None):
         _check(lib.spm_apply_A(self.h, _prec_of(x), _ptr(x), _ptr(y), _nrhs(x, self.n), _stream(stream)))
@@ -204,6 +233,16 @@ class Problem:
 
     def factor_S(self, prec=SPM_C128):
         _check(lib.spm_factor_S(self.h, prec))
+
+    def factor_S_tree(self, prec, variant):
+        """Factor on one nested-dissection tree variant (0..3), no retry."""
+        _check(lib.spm_factor_S_tree(self.h, prec, int(variant)))
+
+    def factor_info(self, prec=SPM_C64):
+        """(variant, attempts, half_store, probe_relres, raised_pivots) of the current factor in ``prec``."""
+        r = FactorReport()
+        _check(lib.spm_factor_info(self.h, prec, ctypes.byref(r)))
+        return r.variant, r.attempts, bool(r.half_store), r.probe_relres, r.raised_pivots
 
     def apply_S(self, x, y, stream=None):
         _check(lib.spm_apply_S(self.h, _prec_of(x), _ptr(x), _ptr(y), _nrhs(x, self.n), _stream(stream)))

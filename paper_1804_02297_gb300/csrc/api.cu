@@ -195,6 +195,8 @@ extern "C" spm_status spm_create_problem(int n, double omega, const double *eps_
         if (P->chunk64 > 64) P->chunk64 = 64;
         if (P->chunk128 > 64) P->chunk128 = 64;
     }
+    if ((st = P->dev_err.ensure(sizeof(int))) != SPM_OK) return fail(st);
+    if (cudaMemset(P->dev_err.ptr, 0, sizeof(int)) != cudaSuccess) { spm_set_error("memset failed"); return fail(SPM_ERR_CUDA); }
     if ((st = spm_build_spectra(P)) != SPM_OK) return fail(st);
     *out = P;
     return SPM_OK;
@@ -207,7 +209,7 @@ extern "C" spm_status spm_destroy(spm_problem P)
     P->spec128.release(); P->spec64.release(); P->tw128.release(); P->tw64.release();
     P->work.release(); P->alpha128.release(); P->alpha64.release(); P->beta128.release();
     P->qtab128.release(); P->qtab64.release();
-    P->S128.release(); P->S64.release(); P->kry.release();
+    P->S128.release(); P->S64.release(); P->kry.release(); P->dev_err.release();
     spm_factor_free(P->fac128);
     spm_factor_free(P->fac64);
     delete P;
@@ -228,7 +230,7 @@ static spm_status check_apply(spm_problem P, spm_prec prec, const void *x, void 
 {
     if (!P) { spm_set_error("NULL problem"); return SPM_ERR_INVALID_ARG; }
     if (!prec_ok(prec)) { spm_set_error("apply precision must be SPM_C128 or SPM_C64"); return SPM_ERR_INVALID_ARG; }
-    if (nrhs < 0) { spm_set_error("nrhs < 0"); return SPM_ERR_INVALID_ARG; }
+    if (nrhs < 0 || nrhs > 65535) { spm_set_error("nrhs must be in [0, 65535]"); return SPM_ERR_INVALID_ARG; }
     if (nrhs > 0 && (!x || !y)) { spm_set_error("NULL buffer"); return SPM_ERR_INVALID_ARG; }
     if (x == y && nrhs > 0) { spm_set_error("input and output alias"); return SPM_ERR_INVALID_ARG; }
     return SPM_OK;
@@ -311,6 +313,54 @@ extern "C" spm_status spm_factor_S(spm_problem P, spm_prec prec)
     if (!prec_ok(prec) && prec != SPM_C64H) { spm_set_error("factor precision must be SPM_C128, SPM_C64 or SPM_C64H"); return SPM_ERR_INVALID_ARG; }
     if (!P->have_S) { spm_set_error("S not assembled"); return SPM_ERR_NOT_BUILT; }
     return spm_factor_impl(P, prec);
+}
+
+extern "C" spm_status spm_get_apply_plan(spm_prec prec, int L, int *zvariant)
+{
+    if (!zvariant || (prec != SPM_C128 && prec != SPM_C64)) { spm_set_error("bad arguments"); return SPM_ERR_INVALID_ARG; }
+    return spm_apply_plan_impl(prec, L, zvariant, nullptr);
+}
+
+extern "C" spm_status spm_set_apply_plan(spm_prec prec, int L, int zvariant)
+{
+    if (prec != SPM_C128 && prec != SPM_C64) { spm_set_error("apply precision must be SPM_C128 or SPM_C64"); return SPM_ERR_INVALID_ARG; }
+    return spm_apply_plan_impl(prec, L, nullptr, &zvariant);
+}
+
+extern "C" spm_status spm_device_status(spm_problem P)
+{
+    if (!P) { spm_set_error("NULL problem"); return SPM_ERR_INVALID_ARG; }
+    SPM_CUDA_TRY(cudaDeviceSynchronize());
+    int flag = 0;
+    SPM_CUDA_TRY(cudaMemcpy(&flag, P->dev_err.ptr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        SPM_CUDA_TRY(cudaMemset(P->dev_err.ptr, 0, sizeof(int)));
+        spm_set_error("a bounded device wait gave up (code %d); the results of that launch are invalid", flag);
+        return SPM_ERR_TIMEOUT;
+    }
+    return SPM_OK;
+}
+
+extern "C" spm_status spm_factor_S_tree(spm_problem P, spm_prec prec, int variant)
+{
+    if (!P) { spm_set_error("NULL problem"); return SPM_ERR_INVALID_ARG; }
+    if (!prec_ok(prec) && prec != SPM_C64H) { spm_set_error("factor precision must be SPM_C128, SPM_C64 or SPM_C64H"); return SPM_ERR_INVALID_ARG; }
+    if (!P->have_S) { spm_set_error("S not assembled"); return SPM_ERR_NOT_BUILT; }
+    return spm_factor_tree_impl(P, prec, variant);
+}
+
+extern "C" spm_status spm_factor_info(spm_problem P, spm_prec prec, spm_factor_report *out)
+{
+    if (!P || !out) { spm_set_error("NULL argument"); return SPM_ERR_INVALID_ARG; }
+    if (prec != SPM_C128 && prec != SPM_C64 && prec != SPM_C64H) { spm_set_error("factor precision must be SPM_C128, SPM_C64 or SPM_C64H"); return SPM_ERR_INVALID_ARG; }
+    const int fi = prec == SPM_C128 ? 0 : 1;
+    if (!(fi == 0 ? P->fac128 : P->fac64)) { spm_set_error("no factor of S in this precision (spm_factor_S)"); return SPM_ERR_NOT_BUILT; }
+    out->variant = P->fac_info[fi].variant;
+    out->attempts = P->fac_info[fi].attempts;
+    out->half_store = P->fac_info[fi].half_store ? 1 : 0;
+    out->probe_relres = P->fac_info[fi].probe_relres;
+    out->raised_pivots = P->fac_info[fi].raised_pivots;
+    return SPM_OK;
 }
 
 extern "C" spm_status spm_apply_S(spm_problem P, spm_prec prec, const void *x, void *y, int nrhs, void *stream)

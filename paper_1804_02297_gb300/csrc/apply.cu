@@ -14,6 +14,9 @@
 //   xinv : inverse FFT along xi, keep x < n, y = x + result
 // The kernel spectra are stored as one octant [4][n+1]^3: Ghat is even in each
 // frequency, Ghat^d is odd in frequency d and even in the others.
+#include <cuda.h> // CUtensorMap (the encoder is reached through the runtime, no libcuda link)
+
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -74,6 +77,8 @@ template <typename R, int L> struct tx_of {
     static constexpr int w = (sizeof(R) == 4 ? 16 : 8) / (L >= 512 ? 2 : 1);
     static constexpr int v = w < L ? w : L; // never wider than a row of L elements
 };
+
+constexpr int ZPROD_FOUR = 0, ZPROD_ONE = 1, ZPROD_TMA = 2; // z-pass kernel choices
 
 template <int L> __device__ __forceinline__ int xpad(int pos) { return pos + (pos >> 3); }
 
@@ -335,16 +340,222 @@ __global__ void __launch_bounds__(256) k2_xinv(const typename cplx_of<R>::type *
     }
 }
 
+
 template <typename K> void allow_smem(K kernel, size_t bytes)
 {
     if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// ---------------------------------------------------------------- TMA z-pass
+// mbarrier and bulk-tensor copy primitives (PTX ISA, sm_90 and later)
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// bounded wait for phase `parity`: about 2^22 polls (each may suspend briefly)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
+{
+    const unsigned a = smem_u32(bar);
+    for (int it = 0; it < (1 << 22); ++it) {
+        unsigned done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done)
+                     : "r"(a), "r"(parity)
+                     : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(
+                     smem_u32(dst)),
+                 "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// zpass fed by TMA: a persistent grid walks the tiles (TX adjacent columns of
+// one right-hand side); while a tile is transformed, the next tile's four
+// fields (n z-values x TX columns each, the pruned half) stream into the other
+// of two shared-memory stages through cp.async.bulk.tensor, completion counted
+// on that stage's mbarrier.  Per tile: forward z-transform of p.E, then per d
+// forward transform, Fourier-side product, inverse transform, z < n stored in
+// place (fields 0..2), as in the other z-pass kernels.  Tensor map: W2 viewed as
+// [nb 4 n][L][L x (complex size / 8)] 8-byte words, box {TX words, 1, n}.
 template <typename R, int L>
-void apply_chunk_v2(const typename cplx_of<R>::type *xb, typename cplx_of<R>::type *yb,
+__global__ void __launch_bounds__(tx_of<R, L>::v * L / line_elems(L)) k2_ztma(const __grid_constant__ CUtensorMap tmap,
+                                                                            typename cplx_of<R>::type *W2,
+                                                                            const typename cplx_of<R>::type *__restrict__ spec,
+                                                                            const typename cplx_of<R>::type *__restrict__ tw,
+                                                                            int ntiles, int tiles_per_rhs, int *err)
+{
+    using C = typename cplx_of<R>::type;
+    constexpr int E = line_elems(L), H = E / 2;
+    constexpr int T = L / E, TX = tx_of<R, L>::v, n = L / 2, n1 = n + 1;
+    constexpr long L2 = (long)L * L, oct = (long)n1 * n1 * n1, fs = (long)n * L * L;
+    constexpr int STAGE = 4 * n * TX;
+    constexpr unsigned STAGE_BYTES = STAGE * sizeof(C);
+    constexpr int WPC = sizeof(C) / 8; // 8-byte words per complex
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    C *stages = reinterpret_cast<C *>(smem_raw);
+    C *xch = stages + 2 * STAGE; // exchange buffer [L][TX]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(xch + L * TX);
+    const int c = threadIdx.x % TX, t = threadIdx.x / TX;
+    auto issue = [&](int tile, int st) { // thread 0
+        const int b = tile / tiles_per_rhs;
+        const long col0 = (long)(tile % tiles_per_rhs) * TX;
+        const int eta = (int)(col0 / L), xi0 = (int)(col0 % L);
+        mbar_expect_tx(&bar[st], STAGE_BYTES);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            const int f = g == 0 ? 3 : g - 1; // consumption order: p.E first
+            tma_load_3d(stages + st * STAGE + g * n * TX, &tmap, xi0 * WPC, eta, (b * 4 + f) * n, &bar[st]);
+        }
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if ((int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
+        if ((int)(blockIdx.x + gridDim.x) < ntiles) issue(blockIdx.x + gridDim.x, 1);
+    }
+    auto buf = [&](int pos) -> C & { return xch[pos * TX + c]; };
+    auto sync = [&]() { __syncthreads(); };
+    int it = 0;
+    bool failed = false;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        const int st = it & 1;
+        const bool ok = mbar_wait(&bar[st], (it >> 1) & 1);
+        if (__syncthreads_or(!ok)) { failed = true; break; } // every thread leaves together
+        const C *pre = stages + st * STAGE; // [g][z][TX]
+        const int b = tile / tiles_per_rhs;
+        const long col = (long)(tile % tiles_per_rhs) * TX + c;
+        C *base = W2 + (long)b * 4 * fs + col;
+        const int eta = (int)(col / L), xi = (int)(col % L);
+        const int a1 = xi <= n ? xi : L - xi, a2 = eta <= n ? eta : L - eta;
+        C w4[E];
+#pragma unroll
+        for (int q = 0; q < H; ++q) w4[q] = pre[(t + T * q) * TX + c];
+#pragma unroll
+        for (int q = H; q < E; ++q) w4[q] = czero<C>();
+        line_fft<-1, L, true>(w4, t, buf, sync, tw);
+#pragma unroll 1
+        for (int d = 0; d < 3; ++d) {
+            C v[E];
+#pragma unroll
+            for (int q = 0; q < H; ++q) v[q] = pre[((d + 1) * n + t + T * q) * TX + c];
+#pragma unroll
+            for (int q = H; q < E; ++q) v[q] = czero<C>();
+            line_fft<-1, L, true>(v, t, buf, sync, tw);
+            const int fr_fixed = d == 0 ? xi : eta;
+#pragma unroll
+            for (int q = 0; q < E; ++q) {
+                const int zeta = t + T * q;
+                const int a3 = zeta <= n ? zeta : L - zeta;
+                const long o = ((long)a3 * n1 + a2) * n1 + a1;
+                C K0 = spec[o], Kd = spec[(1 + d) * oct + o];
+                const int fr = d == 2 ? zeta : fr_fixed;
+                if (fr > n) { Kd.x = -Kd.x; Kd.y = -Kd.y; }
+                v[q] = cfma(K0, v[q], cmul(Kd, w4[q]));
+            }
+            line_fft<1, L, false>(v, t, buf, sync, tw);
+#pragma unroll
+            for (int q = 0; q < H; ++q) base[d * fs + (long)(t + T * q) * L2] = v[q];
+        }
+        __syncthreads(); // stage st and the exchange buffer are free again
+        if (threadIdx.x == 0 && tile + 2 * (int)gridDim.x < ntiles) issue(tile + 2 * gridDim.x, st);
+    }
+    if (failed && threadIdx.x == 0) {
+        atomicExch(err, 1);
+        // the other stage may still have a copy in flight: wait for it (bounded) before leaving
+        const int nxt = it + 1;
+        if ((int)(blockIdx.x + (unsigned)nxt * gridDim.x) < ntiles) mbar_wait(&bar[nxt & 1], (nxt >> 1) & 1);
+    }
+}
+
+
+// tensor-map encoder from the driver, fetched once through the runtime
+typedef CUresult (*encode_tiled_fn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                    const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+encode_tiled_fn tensor_map_encoder()
+{
+    static encode_tiled_fn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, []() {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<encode_tiled_fn>(p);
+    });
+    return fn;
+}
+
+template <typename R, int L> constexpr size_t ztma_smem()
+{
+    using C = typename cplx_of<R>::type;
+    constexpr int TX = tx_of<R, L>::v, n = L / 2;
+    return sizeof(C) * (2 * 4 * n * TX + L * TX) + 2 * sizeof(uint64_t);
+}
+
+template <typename R, int L>
+spm_status launch_ztma(typename cplx_of<R>::type *W2, const typename cplx_of<R>::type *spec,
+                       const typename cplx_of<R>::type *tw, int nb, int *err, cudaStream_t s)
+{
+    using C = typename cplx_of<R>::type;
+    constexpr int TX = tx_of<R, L>::v, n = L / 2, THR = TX * L / line_elems(L);
+    constexpr int WPC = sizeof(C) / 8;
+    encode_tiled_fn enc = tensor_map_encoder();
+    if (!enc) { spm_set_error("cuTensorMapEncodeTiled is not available"); return SPM_ERR_CUDA; }
+    CUtensorMap map;
+    const cuuint64_t dims[3] = {(cuuint64_t)L * WPC, (cuuint64_t)L, (cuuint64_t)nb * 4 * n};
+    const cuuint64_t strides[2] = {(cuuint64_t)L * sizeof(C), (cuuint64_t)L * L * sizeof(C)};
+    const cuuint32_t box[3] = {(cuuint32_t)(TX * WPC), 1u, (cuuint32_t)n};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, W2, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+        spm_set_error("tensor map for the z-pass rejected (L = %d)", L);
+        return SPM_ERR_CUDA;
+    }
+    constexpr size_t smem = ztma_smem<R, L>();
+    static int grid_per_sm = 0;
+    static int sms = 0;
+    if (!grid_per_sm) {
+        allow_smem(k2_ztma<R, L>, smem);
+        int dev = 0;
+        SPM_CUDA_TRY(cudaGetDevice(&dev));
+        SPM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        int per = 0;
+        SPM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k2_ztma<R, L>, THR, smem));
+        grid_per_sm = per > 0 ? per : 1;
+    }
+    const int tiles_per_rhs = L * L / TX, ntiles = tiles_per_rhs * nb;
+    const int grid = std::min(ntiles, grid_per_sm * sms);
+    k2_ztma<R, L><<<grid, THR, smem, s>>>(map, W2, spec, tw, ntiles, tiles_per_rhs, err);
+    return SPM_OK;
+}
+
+
+template <typename R, int L>
+spm_status apply_chunk_v2(const typename cplx_of<R>::type *xb, typename cplx_of<R>::type *yb,
                     const typename cplx_of<R>::type *m, const typename cplx_of<R>::type *p,
                     const typename cplx_of<R>::type *spec, const typename cplx_of<R>::type *tw,
-                    typename cplx_of<R>::type *W1, typename cplx_of<R>::type *W2, int nb, cudaStream_t s)
+                    typename cplx_of<R>::type *W1, typename cplx_of<R>::type *W2, int nb, int zvar, int *err,
+                    cudaStream_t s)
 {
     using C = typename cplx_of<R>::type;
     constexpr int n = L / 2, T = L / line_elems(L), TX = tx_of<R, L>::v;
@@ -359,7 +570,7 @@ void apply_chunk_v2(const typename cplx_of<R>::type *xb, typename cplx_of<R>::ty
         allow_smem(k2_cols<R, L, -1, true>, sm_cols);
         allow_smem(k2_cols<R, L, 1, false>, sm_cols);
         if constexpr (line_elems(L) == 8) allow_smem(k2_zprod4<R, L>, sm_zprod4);
-        else allow_smem(k2_zprod1<R, L>, sm_zprod);
+        allow_smem(k2_zprod1<R, L>, sm_zprod);
         attrs = true;
     }
     const long n2 = (long)n * n, L2 = (long)L * L;
@@ -370,16 +581,126 @@ void apply_chunk_v2(const typename cplx_of<R>::type *xb, typename cplx_of<R>::ty
     }
     k2_cols<R, L, -1, true><<<dim3(L / TX, n, nb * 4), THR, sm_cols, s>>>(
         W1, W2, L, L, 4, 4 * n2 * L, n2 * L, n * (long)L, 4 * (long)n * L2, (long)n * L2, L2, tw);
-    if constexpr (line_elems(L) == 8)
-        k2_zprod4<R, L><<<dim3((unsigned)(L2 / TX), nb), THR, sm_zprod4, s>>>(W2, spec, tw);
-    else
-        k2_zprod1<R, L><<<dim3((unsigned)(L2 / TX), nb), THR, sm_zprod, s>>>(W2, spec, tw);
+    bool done = false;
+    if constexpr (L >= 32) {
+        if (zvar == ZPROD_TMA) {
+            SPM_TRY((launch_ztma<R, L>(W2, spec, tw, nb, err, s)));
+            done = true;
+        }
+    }
+    if constexpr (line_elems(L) == 8) {
+        if (!done && zvar == ZPROD_FOUR) {
+            k2_zprod4<R, L><<<dim3((unsigned)(L2 / TX), nb), THR, sm_zprod4, s>>>(W2, spec, tw);
+            done = true;
+        }
+    }
+    if (!done) k2_zprod1<R, L><<<dim3((unsigned)(L2 / TX), nb), THR, sm_zprod, s>>>(W2, spec, tw);
     k2_cols<R, L, 1, false><<<dim3(L / TX, n, nb * 3), THR, sm_cols, s>>>(
         W2, W1, n, L, 3, 4 * (long)n * L2, (long)n * L2, L2, 3 * n2 * L, n2 * L, n * (long)L, tw);
     {
         long rows = (long)nb * 3 * n2;
         k2_xinv<R, L><<<(unsigned)((rows + LPB - 1) / LPB), LPB * T, sm_rows, s>>>(W1, xb, yb, rows, tw);
     }
+    return SPM_OK;
+}
+
+template <typename R>
+spm_status run_chunk(int L, const typename cplx_of<R>::type *xb, typename cplx_of<R>::type *yb,
+                     const typename cplx_of<R>::type *m, const typename cplx_of<R>::type *p,
+                     const typename cplx_of<R>::type *spec, const typename cplx_of<R>::type *tw,
+                     typename cplx_of<R>::type *W1, typename cplx_of<R>::type *W2, int nb, int zvar, int *err,
+                     cudaStream_t s)
+{
+    switch (L) {
+    case 8: return apply_chunk_v2<R, 8>(xb, yb, m, p, spec, tw, W1, W2, nb, zvar, err, s);
+    case 16: return apply_chunk_v2<R, 16>(xb, yb, m, p, spec, tw, W1, W2, nb, zvar, err, s);
+    case 32: return apply_chunk_v2<R, 32>(xb, yb, m, p, spec, tw, W1, W2, nb, zvar, err, s);
+    case 64: return apply_chunk_v2<R, 64>(xb, yb, m, p, spec, tw, W1, W2, nb, zvar, err, s);
+    case 128: return apply_chunk_v2<R, 128>(xb, yb, m, p, spec, tw, W1, W2, nb, zvar, err, s);
+    case 256: return apply_chunk_v2<R, 256>(xb, yb, m, p, spec, tw, W1, W2, nb, zvar, err, s);
+    case 512: return apply_chunk_v2<R, 512>(xb, yb, m, p, spec, tw, W1, W2, nb, zvar, err, s);
+    case 96: return apply_chunk_v2<R, 96>(xb, yb, m, p, spec, tw, W1, W2, nb, zvar, err, s);
+    case 192: return apply_chunk_v2<R, 192>(xb, yb, m, p, spec, tw, W1, W2, nb, zvar, err, s);
+    default: spm_set_error("unsupported FFT length %d", L); return SPM_ERR_INVALID_ARG;
+    }
+}
+
+// Apply plan.  The z-pass kernel is the choice with more than one candidate:
+// the four-line kernel (all fields in registers, shared barriers; lengths with
+// 8 elements per thread), the one-field-at-a-time kernel (all four fields
+// prefetched into shared memory by cp.async, then transformed one after
+// another), and the persistent TMA-fed kernel (double-buffered stages, L >= 32).  The first apply of each (length, precision) in the process
+// times both candidates on the caller's own data and keeps the faster for every
+// later apply; during stream capture the default kernel is used untimed.
+std::atomic<int> g_zplan[2][10];
+std::atomic<int> g_zplan_init(0);
+
+int len_index(int L)
+{
+    switch (L) {
+    case 8: return 0; case 16: return 1; case 32: return 2; case 64: return 3; case 128: return 4;
+    case 256: return 5; case 512: return 6; case 96: return 7; case 192: return 8; default: return 9;
+    }
+}
+
+int zplan_get(int prec_idx, int L)
+{
+    int expected = 0;
+    if (g_zplan_init.compare_exchange_strong(expected, 1)) {
+        for (auto &row : g_zplan)
+            for (auto &e : row) e.store(-1);
+        g_zplan_init.store(2);
+    }
+    while (g_zplan_init.load() != 2) {}
+    return g_zplan[prec_idx][len_index(L)].load();
+}
+
+template <typename R>
+spm_status choose_zplan(int L, const typename cplx_of<R>::type *xb, typename cplx_of<R>::type *yb,
+                        const typename cplx_of<R>::type *m, const typename cplx_of<R>::type *p,
+                        const typename cplx_of<R>::type *spec, const typename cplx_of<R>::type *tw,
+                        typename cplx_of<R>::type *W1, typename cplx_of<R>::type *W2, int nb, int *err, cudaStream_t s,
+                        int *zvar)
+{
+    const int pi = sizeof(R) == 8 ? 0 : 1;
+    int z = zplan_get(pi, L);
+    if (z >= 0) { *zvar = z; return SPM_OK; }
+    const int fallback = line_elems(L) == 8 ? ZPROD_FOUR : ZPROD_ONE;
+    int cands[3], nc = 0;
+    if (line_elems(L) == 8) cands[nc++] = ZPROD_FOUR;
+    if (line_elems(L) != 8 || L >= 32) cands[nc++] = ZPROD_ONE;
+    if (L >= 32) cands[nc++] = ZPROD_TMA;
+    if (nc == 1) { g_zplan[pi][len_index(L)].store(cands[0]); *zvar = cands[0]; return SPM_OK; }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    SPM_CUDA_TRY(cudaStreamIsCapturing(s, &cap));
+    if (cap != cudaStreamCaptureStatusNone) { *zvar = fallback; return SPM_OK; }
+    cudaEvent_t e0, e1;
+    SPM_CUDA_TRY(cudaEventCreate(&e0));
+    SPM_CUDA_TRY(cudaEventCreate(&e1));
+    float best = 0;
+    int best_z = fallback;
+    spm_status st = SPM_OK;
+    for (int ci = 0; ci < nc; ++ci) {
+        const int cand = cands[ci];
+        st = run_chunk<R>(L, xb, yb, m, p, spec, tw, W1, W2, nb, cand, err, s); // warm-up
+        if (st != SPM_OK) break;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 3 && st == SPM_OK; ++r) st = run_chunk<R>(L, xb, yb, m, p, spec, tw, W1, W2, nb, cand, err, s);
+        cudaEventRecord(e1, s);
+        if (st != SPM_OK || cudaEventSynchronize(e1) != cudaSuccess) { st = st != SPM_OK ? st : SPM_ERR_CUDA; break; }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ci == 0 || ms < best) { best = ms; best_z = cand; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != SPM_OK) {
+        if (st == SPM_ERR_CUDA) spm_set_error("timing the z-pass candidates failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return st;
+    }
+    g_zplan[pi][len_index(L)].store(best_z);
+    *zvar = best_z;
+    return SPM_OK;
 }
 
 template <typename R>
@@ -400,57 +721,71 @@ spm_status apply_A_typed(spm_problem_s *P, const void *xv, void *yv, int nrhs, c
     SPM_TRY(P->work.ensure(sizeof(C) * (size_t)chunk * (w1 + w2)));
     C *W1 = P->work.as<C>();
     C *W2 = W1 + (long)chunk * w1;
+    int zvar = ZPROD_FOUR;
+    SPM_TRY(choose_zplan<R>(L, x, y, m, p, spec, tw, W1, W2, nrhs < chunk ? nrhs : chunk, P->dev_err.as<int>(), s, &zvar));
     for (int b0 = 0; b0 < nrhs; b0 += chunk) {
         const int nb = nrhs - b0 < chunk ? nrhs - b0 : chunk;
-        const C *xb = x + (long)b0 * 3 * n3;
-        C *yb = y + (long)b0 * 3 * n3;
-        switch (L) {
-        case 8: apply_chunk_v2<R, 8>(xb, yb, m, p, spec, tw, W1, W2, nb, s); break;
-        case 16: apply_chunk_v2<R, 16>(xb, yb, m, p, spec, tw, W1, W2, nb, s); break;
-        case 32: apply_chunk_v2<R, 32>(xb, yb, m, p, spec, tw, W1, W2, nb, s); break;
-        case 64: apply_chunk_v2<R, 64>(xb, yb, m, p, spec, tw, W1, W2, nb, s); break;
-        case 128: apply_chunk_v2<R, 128>(xb, yb, m, p, spec, tw, W1, W2, nb, s); break;
-        case 256: apply_chunk_v2<R, 256>(xb, yb, m, p, spec, tw, W1, W2, nb, s); break;
-        case 512: apply_chunk_v2<R, 512>(xb, yb, m, p, spec, tw, W1, W2, nb, s); break;
-        case 96: apply_chunk_v2<R, 96>(xb, yb, m, p, spec, tw, W1, W2, nb, s); break;
-        case 192: apply_chunk_v2<R, 192>(xb, yb, m, p, spec, tw, W1, W2, nb, s); break;
-        default: spm_set_error("unsupported FFT length %d", L); return SPM_ERR_INVALID_ARG;
-        }
+        SPM_TRY(run_chunk<R>(L, x + (long)b0 * 3 * n3, y + (long)b0 * 3 * n3, m, p, spec, tw, W1, W2, nb, zvar, P->dev_err.as<int>(), s));
     }
     SPM_CUDA_TRY(cudaGetLastError());
     return SPM_OK;
 }
 
-// Q gather in two launches.
-// Interior points (1 <= i_d <= n-2, one class): a block owns a 32 x 4 x 2 tile
-// whose three components plus a one-point halo are staged in shared memory; the
-// class's 243 coefficients arrive as a by-value kernel parameter, so they sit in
-// the constant bank and enter the FMAs as operands without load instructions.
-// Boundary shell (at least one i_d in {0, n-1}, 26 classes): one warp per
-// point below, coefficients from the expanded table [cls][d][o][c] (zero
-// outside the class neighbourhood).
+// Q gather in one launch of 256-thread blocks of three kinds (block-uniform
+// branch), boundary blocks first so that their latency overlaps the interior:
+// * face blocks: the points with exactly one coordinate on the boundary belong
+//   to one of six face classes; a block owns a 32 x 8 tile of one face, stages
+//   the face layer and the next layer inward (three components, one-point halo)
+//   and its class's 18-neighbour coefficients (remapped to face-local order) in
+//   shared memory, and each thread forms its point's three outputs;
+// * edge blocks: the 12 (n-2) + 8 points on edges and corners, one warp per
+//   point; lane l takes the terms (d, o) with d * 27 + o in {l, l + 32, l + 64}
+//   (of 81) from the expanded table [cls][d][o][c] (zero outside the class
+//   neighbourhood, which is also where a neighbour would leave the grid) and
+//   the warp sums its partials;
+// * interior blocks (1 <= i_d <= n-2, one class): a 32 x 4 x 2 tile whose three
+//   components plus a one-point halo are staged in shared memory; the class's
+//   243 coefficients arrive as a by-value kernel parameter, so they sit in the
+//   constant bank and enter the FMAs as operands without load instructions.
+constexpr int Q_THREADS = 256;
 constexpr int QX = 32, QY = 4, QZ = 2;
 constexpr int QHX = QX + 2, QHY = QY + 2, QHZ = QZ + 2, QH = QHX * QHY * QHZ;
+constexpr int QF_U = 32, QF_W = 8;
+constexpr int QF_HU = QF_U + 2, QF_HW = QF_W + 2, QF_HALO = 3 * 2 * QF_HW * QF_HU;
+constexpr int Q_SMEM = (3 * QH > QF_HALO + 162) ? 3 * QH : QF_HALO + 162; // complex elements
+static_assert(QX * QY * QZ == Q_THREADS && QF_U * QF_W == Q_THREADS, "Q block shapes");
 
 template <typename C> struct QInterior {
     C a[243]; // [d][o][c], o = (o3+1)*9 + (o2+1)*3 + (o1+1)
 };
 
-template <typename R>
-__global__ void __launch_bounds__(QX * QY * QZ) k_q_interior(const typename cplx_of<R>::type *__restrict__ v,
-                                                             const QInterior<typename cplx_of<R>::type> qa,
-                                                             typename cplx_of<R>::type *__restrict__ y, int n)
+// edge point number e (0 <= e < 12 (n-2) + 8) -> (i1, i2, i3): corners, then the
+// edges along x, y, z (four each)
+__device__ __forceinline__ void edge_point(int e, int n, int &i1, int &i2, int &i3)
 {
-    using C = typename cplx_of<R>::type;
-    __shared__ C sv[3 * QH];
+    if (e < 8) {
+        i1 = (e & 1) ? n - 1 : 0;
+        i2 = (e & 2) ? n - 1 : 0;
+        i3 = (e & 4) ? n - 1 : 0;
+        return;
+    }
+    const int r = e - 8, k = r / (n - 2), t = 1 + r % (n - 2);
+    const int a = k >> 2, b0 = (k & 1) ? n - 1 : 0, b1 = (k & 2) ? n - 1 : 0;
+    if (a == 0) { i1 = t; i2 = b0; i3 = b1; }
+    else if (a == 1) { i1 = b0; i2 = t; i3 = b1; }
+    else { i1 = b0; i2 = b1; i3 = t; }
+}
+
+template <typename C>
+__device__ __forceinline__ void q_interior_block(int blk, const C *__restrict__ vb, const QInterior<C> &qa,
+                                                 C *__restrict__ yb, int n, C *sv)
+{
     const long n3 = (long)n * n * n;
     const int m = n - 2; // interior extent
-    const int tiles_x = (m + QX - 1) / QX;
-    const int tx0 = 1 + (blockIdx.x % tiles_x) * QX, ty0 = 1 + (blockIdx.x / tiles_x) * QY;
-    const int tz0 = 1 + blockIdx.y * QZ;
-    const long b = blockIdx.z;
-    const C *vb = v + b * 3 * n3;
-    for (int i = threadIdx.x; i < 3 * QH; i += blockDim.x) {
+    const int tiles_x = (m + QX - 1) / QX, tiles_y = (m + QY - 1) / QY;
+    const int txy = blk % (tiles_x * tiles_y), tz = blk / (tiles_x * tiles_y);
+    const int tx0 = 1 + (txy % tiles_x) * QX, ty0 = 1 + (txy / tiles_x) * QY, tz0 = 1 + tz * QZ;
+    for (int i = threadIdx.x; i < 3 * QH; i += Q_THREADS) {
         int d = i / QH, h = i % QH;
         int hx = h % QHX, hy = (h / QHX) % QHY, hz = h / (QHX * QHY);
         int gx = tx0 + hx - 1, gy = ty0 + hy - 1, gz = tz0 + hz - 1;
@@ -480,61 +815,87 @@ __global__ void __launch_bounds__(QX * QY * QZ) k_q_interior(const typename cplx
                 }
     }
     const long i = ((long)i3 * n + i2) * n + i1;
-    C *yb = y + b * 3 * n3;
     yb[i] = acc0;
     yb[n3 + i] = acc1;
     yb[2 * n3 + i] = acc2;
 }
 
-// shell point number e (0 <= e < 6n^2 - 12n + 8) -> (i1, i2, i3): the two z faces,
-// then the two y faces of the interior z range, then the two x faces of the
-// interior (y, z) range
-__device__ __forceinline__ void shell_point(long e, int n, int &i1, int &i2, int &i3)
+template <typename C>
+__device__ __forceinline__ void q_face_block(int blk, const C *__restrict__ vb, const C *__restrict__ qtab,
+                                             C *__restrict__ yb, int n, C *sv)
 {
-    const long n2 = (long)n * n, zf = 2 * n2, yf = 2L * n * (n - 2);
-    if (e < zf) {
-        i3 = e < n2 ? 0 : n - 1;
-        const long r = e % n2;
-        i2 = (int)(r / n);
-        i1 = (int)(r % n);
-    } else if (e < zf + yf) {
-        const long r = e - zf, half = (long)n * (n - 2);
-        i2 = r < half ? 0 : n - 1;
-        const long q = r % half;
-        i3 = 1 + (int)(q / n);
-        i1 = (int)(q % n);
-    } else {
-        const long r = e - zf - yf;
-        i1 = (r & 1) ? n - 1 : 0;
-        const long q = r >> 1;
-        i2 = 1 + (int)(q % (n - 2));
-        i3 = 1 + (int)(q / (n - 2));
+    C *sa = sv + QF_HALO; // 162 coefficients [d][la][ou][ow][c]
+    const long n3 = (long)n * n * n, n2 = (long)n * n;
+    const int m = n - 2;
+    const int tiles_u = (m + QF_U - 1) / QF_U, tiles_w = (m + QF_W - 1) / QF_W;
+    const int per_face = tiles_u * tiles_w;
+    const int face = blk / per_face, tile = blk % per_face;
+    const int a = face >> 1, side = face & 1;          // face i_a = 0 (side 0) or n-1 (side 1)
+    const int ua = a == 0 ? 1 : 0, wa = a == 2 ? 1 : 2; // the face's in-plane axes, ascending
+    const int inward = side ? -1 : 1;
+    const int u0 = (tile % tiles_u) * QF_U, w0 = (tile / tiles_u) * QF_W; // halo origin (grid coords)
+    const long sa_ = a == 0 ? 1 : (a == 1 ? n : n2); // strides of the face normal and in-plane axes
+    const long su = ua == 0 ? 1 : n, sw = wa == 1 ? n : n2;
+    const int ia0 = side ? n - 1 : 0;
+    const int cf = side ? 2 : 0;
+    const int cls = (a == 0 ? cf : 1) + 3 * (a == 1 ? cf : 1) + 9 * (a == 2 ? cf : 1);
+    const C *al = qtab + (long)cls * 243;
+    for (int i = threadIdx.x; i < 162; i += Q_THREADS) {
+        const int c = i % 3, l = (i / 3) % 18, d = i / 54;
+        const int la = l / 9, ou = (l / 3) % 3 - 1, ow = l % 3 - 1;
+        const int on = la ? inward : 0;
+        const int o1 = a == 0 ? on : ou;
+        const int o2 = a == 1 ? on : (a == 0 ? ou : ow);
+        const int o3 = a == 2 ? on : ow;
+        const int o = (o3 + 1) * 9 + (o2 + 1) * 3 + (o1 + 1);
+        sa[i] = al[(d * 27 + o) * 3 + c];
     }
+    for (int i = threadIdx.x; i < QF_HALO; i += Q_THREADS) {
+        const int hu = i % QF_HU, hw = (i / QF_HU) % QF_HW, la = (i / (QF_HU * QF_HW)) % 2, d = i / (2 * QF_HU * QF_HW);
+        const int gu = u0 + hu, gw = w0 + hw; // halo starts one point before the first face point (u = 1)
+        C val = czero<C>();
+        if (gu < n && gw < n) val = vb[d * n3 + (ia0 + (la ? inward : 0)) * sa_ + gu * su + gw * sw];
+        sv[i] = val;
+    }
+    __syncthreads();
+    const int lu = threadIdx.x % QF_U, lw = threadIdx.x / QF_U;
+    const int pu = 1 + u0 + lu, pw = 1 + w0 + lw;
+    if (pu > m || pw > m) return;
+    C acc0 = czero<C>(), acc1 = czero<C>(), acc2 = czero<C>();
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int la = 0; la < 2; ++la)
+#pragma unroll
+            for (int ou = -1; ou <= 1; ++ou)
+#pragma unroll
+                for (int ow = -1; ow <= 1; ++ow) {
+                    const C val = sv[((d * 2 + la) * QF_HW + (lw + 1 + ow)) * QF_HU + (lu + 1 + ou)];
+                    const C *ar = sa + ((d * 18 + la * 9 + (ou + 1) * 3 + (ow + 1)) * 3);
+                    acc0 = cfma(ar[0], val, acc0);
+                    acc1 = cfma(ar[1], val, acc1);
+                    acc2 = cfma(ar[2], val, acc2);
+                }
+    const long i = ia0 * sa_ + pu * su + pw * sw;
+    yb[i] = acc0;
+    yb[n3 + i] = acc1;
+    yb[2 * n3 + i] = acc2;
 }
 
-// Boundary shell: one warp per shell point; lane l takes the terms (d, o) with
-// d * 27 + o in {l, l + 32, l + 64} (of 81), then the warp sums its partials.
-// Coefficients come from the expanded table (zero outside the neighbourhood,
-// which is also where a neighbour would leave the grid).
-template <typename R>
-__global__ void __launch_bounds__(256) k_q_shell(const typename cplx_of<R>::type *__restrict__ v,
-                                                 const typename cplx_of<R>::type *__restrict__ qtab,
-                                                 typename cplx_of<R>::type *__restrict__ y, int n, long per_rhs,
-                                                 int nrhs)
+template <typename C>
+__device__ __forceinline__ void q_edge_block(int blk, const C *__restrict__ vb, const C *__restrict__ qtab,
+                                             C *__restrict__ yb, int n, int nedge)
 {
-    using C = typename cplx_of<R>::type;
-    const long w = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (w >= per_rhs * nrhs) return; // whole warps leave together
     const long n3 = (long)n * n * n;
-    const long b = w / per_rhs;
+    const int e = blk * (Q_THREADS / 32) + (int)(threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (e >= nedge) return; // whole warps leave together
     int i1, i2, i3;
-    shell_point(w - b * per_rhs, n, i1, i2, i3);
+    edge_point(e, n, i1, i2, i3);
     const int c1 = i1 == 0 ? 0 : (i1 == n - 1 ? 2 : 1);
     const int c2 = i2 == 0 ? 0 : (i2 == n - 1 ? 2 : 1);
     const int c3 = i3 == 0 ? 0 : (i3 == n - 1 ? 2 : 1);
     const C *al = qtab + (long)(c1 + 3 * c2 + 9 * c3) * 243;
-    const C *vb = v + b * 3 * n3;
     C acc0 = czero<C>(), acc1 = czero<C>(), acc2 = czero<C>();
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -560,11 +921,29 @@ __global__ void __launch_bounds__(256) k_q_shell(const typename cplx_of<R>::type
     }
     if (lane == 0) {
         const long i = ((long)i3 * n + i2) * n + i1;
-        C *yb = y + b * 3 * n3;
         yb[i] = acc0;
         yb[n3 + i] = acc1;
         yb[2 * n3 + i] = acc2;
     }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(Q_THREADS) k_q(const typename cplx_of<R>::type *__restrict__ v,
+                                                 const QInterior<typename cplx_of<R>::type> qa,
+                                                 const typename cplx_of<R>::type *__restrict__ qtab,
+                                                 typename cplx_of<R>::type *__restrict__ y, int n, int face_blocks,
+                                                 int edge_blocks, int nedge)
+{
+    using C = typename cplx_of<R>::type;
+    __shared__ C sv[Q_SMEM];
+    const long n3 = (long)n * n * n;
+    const long b = blockIdx.y;
+    const C *vb = v + b * 3 * n3;
+    C *yb = y + b * 3 * n3;
+    const int blk = blockIdx.x;
+    if (blk < face_blocks) q_face_block<C>(blk, vb, qtab, yb, n, sv);
+    else if (blk < face_blocks + edge_blocks) q_edge_block<C>(blk - face_blocks, vb, qtab, yb, n, nedge);
+    else q_interior_block<C>(blk - face_blocks - edge_blocks, vb, qa, yb, n, sv);
 }
 
 template <typename R>
@@ -582,11 +961,12 @@ spm_status apply_Q_typed(spm_problem_s *P, const void *vv, void *yv, int nrhs, c
     const C *v = reinterpret_cast<const C *>(vv);
     C *y = reinterpret_cast<C *>(yv);
     const int m = n - 2;
-    const int tiles_x = (m + QX - 1) / QX, tiles_y = (m + QY - 1) / QY;
-    dim3 grid((unsigned)(tiles_x * tiles_y), (unsigned)((m + QZ - 1) / QZ), (unsigned)nrhs);
-    k_q_interior<R><<<grid, QX * QY * QZ, 0, s>>>(v, qa, y, n);
-    const long shell = 6L * n * n - 12L * n + 8;
-    k_q_shell<R><<<(unsigned)((shell * nrhs * 32 + 255) / 256), 256, 0, s>>>(v, qtab, y, n, shell, nrhs);
+    const int interior_blocks = ((m + QX - 1) / QX) * ((m + QY - 1) / QY) * ((m + QZ - 1) / QZ);
+    const int face_blocks = 6 * ((m + QF_U - 1) / QF_U) * ((m + QF_W - 1) / QF_W);
+    const int nedge = 12 * m + 8;
+    const int edge_blocks = (nedge + Q_THREADS / 32 - 1) / (Q_THREADS / 32);
+    k_q<R><<<dim3((unsigned)(face_blocks + edge_blocks + interior_blocks), (unsigned)nrhs), Q_THREADS, 0, s>>>(
+        v, qa, qtab, y, n, face_blocks, edge_blocks, nedge);
     SPM_CUDA_TRY(cudaGetLastError());
     return SPM_OK;
 }
@@ -625,6 +1005,29 @@ spm_status spm_build_qtable(spm_problem_s *P)
     SPM_TRY(P->qtab64.ensure(sizeof(float) * t32.size()));
     SPM_CUDA_TRY(cudaMemcpy(P->qtab128.ptr, t.data(), sizeof(double) * t.size(), cudaMemcpyHostToDevice));
     SPM_CUDA_TRY(cudaMemcpy(P->qtab64.ptr, t32.data(), sizeof(float) * t32.size(), cudaMemcpyHostToDevice));
+    return SPM_OK;
+}
+
+// supported z-pass kernels of a length: bit v set if variant v can run
+static int zplan_supported(int L)
+{
+    const bool e8 = !(L == 96 || L == 192);
+    return (e8 ? 1 << ZPROD_FOUR : 0) | ((!e8 || L >= 32) ? 1 << ZPROD_ONE : 0) | (L >= 32 ? 1 << ZPROD_TMA : 0);
+}
+
+spm_status spm_apply_plan_impl(int prec, int L, int *get, const int *set)
+{
+    if (len_index(L) > 8) { spm_set_error("no apply plan for FFT length %d", L); return SPM_ERR_INVALID_ARG; }
+    const int pi = prec == SPM_C128 ? 0 : 1;
+    if (set) {
+        if (*set != -1 && (*set < 0 || *set > 2 || !(zplan_supported(L) & (1 << *set)))) {
+            spm_set_error("z-pass variant %d is not available for FFT length %d", *set, L);
+            return SPM_ERR_INVALID_ARG;
+        }
+        zplan_get(pi, L); // initialise the table
+        g_zplan[pi][len_index(L)].store(*set);
+    }
+    if (get) *get = zplan_get(pi, L);
     return SPM_OK;
 }
 
@@ -874,22 +1277,14 @@ spm_status apply_A_noalloc_typed(spm_problem_s *P, const void *xv, void *yv, int
     const C *x = reinterpret_cast<const C *>(xv);
     C *y = reinterpret_cast<C *>(yv);
     // Every pass writes its whole output before the next pass reads it, so no
-    // part of the shared scratch has to be cleared between calls.
+    // part of the shared scratch has to be cleared between calls.  The z-pass
+    // kernel is the one the timed applies chose, if any (no timing here).
+    const int zcached = zplan_get(dbl ? 0 : 1, L);
+    const int zvar = zcached >= 0 ? zcached : (L == 96 || L == 192 ? ZPROD_ONE : ZPROD_FOUR);
     for (int b = 0; b < nrhs; ++b) {
         const C *xb = x + (long)b * 3 * n3;
         C *yb = y + (long)b * 3 * n3;
-        switch (L) {
-        case 8: apply_chunk_v2<R, 8>(xb, yb, m, p, spec, tw, W1, W2, 1, s); break;
-        case 16: apply_chunk_v2<R, 16>(xb, yb, m, p, spec, tw, W1, W2, 1, s); break;
-        case 32: apply_chunk_v2<R, 32>(xb, yb, m, p, spec, tw, W1, W2, 1, s); break;
-        case 64: apply_chunk_v2<R, 64>(xb, yb, m, p, spec, tw, W1, W2, 1, s); break;
-        case 128: apply_chunk_v2<R, 128>(xb, yb, m, p, spec, tw, W1, W2, 1, s); break;
-        case 256: apply_chunk_v2<R, 256>(xb, yb, m, p, spec, tw, W1, W2, 1, s); break;
-        case 512: apply_chunk_v2<R, 512>(xb, yb, m, p, spec, tw, W1, W2, 1, s); break;
-        case 96: apply_chunk_v2<R, 96>(xb, yb, m, p, spec, tw, W1, W2, 1, s); break;
-        case 192: apply_chunk_v2<R, 192>(xb, yb, m, p, spec, tw, W1, W2, 1, s); break;
-        default: spm_set_error("unsupported FFT length %d", L); return SPM_ERR_INVALID_ARG;
-        }
+        SPM_TRY(run_chunk<R>(L, xb, yb, m, p, spec, tw, W1, W2, 1, zvar, P->dev_err.as<int>(), s));
     }
     SPM_CUDA_TRY(cudaGetLastError());
     return SPM_OK;

@@ -126,6 +126,7 @@ struct spm_problem_s {
     DevBuf tw128, tw64;
     // apply workspace
     DevBuf work;
+    DevBuf dev_err; // int: set by a kernel whose bounded wait gave up (SPM_ERR_TIMEOUT)
     int chunk128 = 1, chunk64 = 1; // right-hand sides per pass chunk
 
     // stencils
@@ -138,6 +139,8 @@ struct spm_problem_s {
     bool have_S = false;
     DevBuf S128, S64; // [n^3][27][3][3] complex; absent neighbours hold zeros
     NDFactor *fac128 = nullptr, *fac64 = nullptr;
+    struct FactorInfo { int variant = -1, attempts = 0, raised_pivots = 0; double probe_relres = 0; bool half_store = false; };
+    FactorInfo fac_info[2]; // [0] complex128 factor, [1] complex64 factor
 
     // solver workspace
     DevBuf kry;
@@ -146,12 +149,14 @@ struct spm_problem_s {
 // ------------------------------------------------------------ internal API
 spm_status spm_apply_A_impl(spm_problem_s *P, int prec, const void *x, void *y, int nrhs, cudaStream_t s);
 spm_status spm_apply_Q_impl(spm_problem_s *P, int prec, const void *v, void *y, int nrhs, cudaStream_t s);
+spm_status spm_apply_plan_impl(int prec, int L, int *get, const int *set);
 spm_status spm_build_qtable(spm_problem_s *P);
 spm_status spm_build_spectra(spm_problem_s *P);
 spm_status spm_stencils_device(spm_problem_s *P);
 spm_status spm_assemble_S(spm_problem_s *P);
 spm_status spm_apply_S_impl(spm_problem_s *P, int prec, const void *x, void *y, int nrhs, cudaStream_t s);
 spm_status spm_factor_impl(spm_problem_s *P, int prec);
+spm_status spm_factor_tree_impl(spm_problem_s *P, int prec, int variant);
 spm_status spm_solveS_impl(spm_problem_s *P, int prec, const void *b, void *x, int nrhs, cudaStream_t s);
 void spm_factor_free(NDFactor *f);
 spm_status spm_solve_impl(spm_problem_s *P, int prec, const void *g, void *x, int nrhs, double tol,

@@ -29,6 +29,7 @@
 #include <cusolverDn.h>
 
 #include <algorithm>
+#include <cmath>
 #include <type_traits>
 #include <vector>
 
@@ -151,6 +152,46 @@ template <typename C> __global__ void k_identity(C *a, int n, int ld)
     int r = (int)(gid % n), c = (int)(gid / n);
     a[(long)c * ld + r].x = r == c ? 1 : 0;
     a[(long)c * ld + r].y = 0;
+}
+
+// Static pivot perturbation.  Pivoting stays inside each front's fully summed
+// block F11, so a box of the dissection whose part of S is (nearly) singular
+// leaves tiny pivots in U even when S is well conditioned, and every later
+// Schur complement then carries their reciprocal.  After the partial-pivoting
+// LU of F11, each |U_ii| below tau * max_j |U_jj| is raised to that size, phase
+// kept: the factor becomes exact for S plus a perturbation of rank equal to the
+// number of raised pivots (counted in *count), which GMRES on the
+// preconditioned system absorbs in about that many extra iterations.
+template <typename C> __global__ void __launch_bounds__(1024) k_perturb_pivots(C *lu, int ld, int nd, double tau, int *count)
+{
+    __shared__ double red[32];
+    double mx = 0;
+    for (int i = threadIdx.x; i < nd; i += blockDim.x) {
+        const C u = lu[(long)i * ld + i];
+        mx = fmax(mx, sqrt((double)u.x * u.x + (double)u.y * u.y));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        mx = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (threadIdx.x == 0) red[0] = mx;
+    }
+    __syncthreads();
+    const double floor_ = tau * red[0];
+    int raised = 0;
+    for (int i = threadIdx.x; i < nd; i += blockDim.x) {
+        C &u = lu[(long)i * ld + i];
+        const double a = sqrt((double)u.x * u.x + (double)u.y * u.y);
+        if (a < floor_) {
+            const double sx = a > 0 ? u.x / a : 1.0, sy = a > 0 ? u.y / a : 0.0;
+            u.x = (decltype(u.x))(floor_ * sx);
+            u.y = (decltype(u.y))(floor_ * sy);
+            ++raised;
+        }
+    }
+    if (raised) atomicAdd(count, raised);
 }
 
 // Level tables.  Per node of a level: its matrix (rows x cols, column-major,
@@ -331,6 +372,8 @@ __global__ void k_level_scatter(C *w, const C *__restrict__ packed, const LevelN
 
 struct NDFactor {
     int prec = 0;
+    int variant = 0;         // nested-dissection tree variant (cut offsets)
+    int raised_pivots = 0;   // pivots raised by the static perturbation
     bool half_store = false; // blocks as scaled binary16 pairs (complex64 factor only)
     DevBuf scales;           // per-column scales (half storage)
     int n = 0;
@@ -371,7 +414,30 @@ namespace {
 
 constexpr int LEAF_SIDE = 5;
 
-int build_tree(std::vector<Node> &nodes, const int lo[3], const int hi[3], int depth = 0)
+// Separator offset of tree variant v at a given depth.  Variant 0 cuts every box
+// through its middle plane; the others move the cuts by one plane (all down,
+// all up, alternating by depth), so that every box of the tree changes.  A box
+// whose restriction of S is nearly singular makes its separator's Schur block
+// nearly singular too (det S_box = det S_children * det F11), and the pivots of
+// the multifrontal LU stay inside each front, so such a box spoils the factor;
+// a different tree has different boxes.
+constexpr int TREE_VARIANTS = 4;
+
+// relative floor of the pivots of a front (about the square root of the
+// precision's unit roundoff: near-singular boxes only, since S itself is well
+// conditioned)
+template <typename R> constexpr double pivot_floor() { return sizeof(R) == 8 ? 1e-8 : 1e-4; }
+inline int cut_offset(int variant, int depth)
+{
+    switch (variant) {
+    case 1: return -1;
+    case 2: return 1;
+    case 3: return (depth & 1) ? 1 : -1;
+    default: return 0;
+    }
+}
+
+int build_tree(std::vector<Node> &nodes, const int lo[3], const int hi[3], int variant, int depth = 0)
 {
     Node nd;
     nd.depth = depth;
@@ -381,12 +447,14 @@ int build_tree(std::vector<Node> &nodes, const int lo[3], const int hi[3], int d
     int len = hi[axis] - lo[axis];
     if (len > LEAF_SIDE) {
         nd.axis = axis;
-        nd.cut = lo[axis] + len / 2;
+        int cut = lo[axis] + len / 2 + cut_offset(variant, depth);
+        cut = std::max(lo[axis] + 1, std::min(hi[axis] - 2, cut)); // both halves non-empty
+        nd.cut = cut;
         int lhi[3] = {hi[0], hi[1], hi[2]}, rlo[3] = {lo[0], lo[1], lo[2]};
         lhi[axis] = nd.cut;
         rlo[axis] = nd.cut + 1;
-        nd.left = build_tree(nodes, lo, lhi, depth + 1);
-        nd.right = build_tree(nodes, rlo, hi, depth + 1);
+        nd.left = build_tree(nodes, lo, lhi, variant, depth + 1);
+        nd.right = build_tree(nodes, rlo, hi, variant, depth + 1);
     }
     nodes.push_back(nd);
     return (int)nodes.size() - 1;
@@ -395,7 +463,7 @@ int build_tree(std::vector<Node> &nodes, const int lo[3], const int hi[3], int d
 } // namespace
 
 template <typename R>
-static spm_status factor_typed(spm_problem_s *P, NDFactor *F, bool half_store)
+static spm_status factor_typed(spm_problem_s *P, NDFactor *F, bool half_store, int variant)
 {
     using BT = blas_t<R>;
     using C = typename BT::C;
@@ -406,7 +474,8 @@ static spm_status factor_typed(spm_problem_s *P, NDFactor *F, bool half_store)
     F->n = n;
     F->nodes.clear();
     int lo[3] = {0, 0, 0}, hi[3] = {n, n, n};
-    build_tree(F->nodes, lo, hi);
+    build_tree(F->nodes, lo, hi, variant);
+    F->variant = variant;
     std::vector<Node> &nodes = F->nodes;
     const int NN = (int)nodes.size();
 
@@ -501,7 +570,7 @@ static spm_status factor_typed(spm_problem_s *P, NDFactor *F, bool half_store)
     SPM_TRY(F->piv.ensure(sizeof(int) * std::max<long>(piv_total, 1)));
     SPM_TRY(F->front.ensure(sizeof(C) * max_f * max_f));
     SPM_TRY(F->stack.ensure(sizeof(C) * std::max<size_t>(max_upd_stack, 1)));
-    SPM_TRY(F->info.ensure(sizeof(int) * 2));
+    SPM_TRY(F->info.ensure(sizeof(int) * 3)); // getrf info, getrs info, raised pivots
     if (!F->cublas && cublasCreate(&F->cublas) != CUBLAS_STATUS_SUCCESS) { spm_set_error("cublasCreate failed"); return SPM_ERR_CUDA; }
     if (!F->cusolver && cusolverDnCreate(&F->cusolver) != CUSOLVER_STATUS_SUCCESS) { spm_set_error("cusolverDnCreate failed"); return SPM_ERR_CUDA; }
     cublasSetStream(F->cublas, s);
@@ -512,7 +581,7 @@ static spm_status factor_typed(spm_problem_s *P, NDFactor *F, bool half_store)
         return SPM_ERR_CUDA;
     }
     SPM_TRY(F->work.ensure(sizeof(C) * std::max(lwork, 1)));
-    SPM_CUDA_TRY(cudaMemsetAsync(F->info.ptr, 0, sizeof(int) * 2, s));
+    SPM_CUDA_TRY(cudaMemsetAsync(F->info.ptr, 0, sizeof(int) * 3, s));
 
     const C *Sdev = reinterpret_cast<const C *>(sizeof(R) == 8 ? P->S128.ptr : P->S64.ptr);
     const int *dpts = F->pts.as<int>(), *dmaps = F->maps.as<int>(), *drels = F->rels.as<int>();
@@ -543,6 +612,7 @@ static spm_status factor_typed(spm_problem_s *P, NDFactor *F, bool half_store)
             spm_set_error("getrf failed at node %d", id);
             return SPM_ERR_CUDA;
         }
+        if (o3 > 0) k_perturb_pivots<C><<<1, 1024, 0, s>>>(front, f, o3, pivot_floor<R>(), dinfo + 2);
         if (b3 > 0) {
             if (BT::getrs(F->cusolver, o3, b3, front, f, dpiv + nd.piv_off, front + (long)o3 * f, f, dinfo + 1) !=
                 CUSOLVER_STATUS_SUCCESS) {
@@ -591,12 +661,13 @@ static spm_status factor_typed(spm_problem_s *P, NDFactor *F, bool half_store)
         }
         SPM_CUDA_TRY(cudaGetLastError());
     }
-    int hinfo[2] = {0, 0};
-    SPM_CUDA_TRY(cudaMemcpyAsync(hinfo, dinfo, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+    int hinfo[3] = {0, 0, 0};
+    SPM_CUDA_TRY(cudaMemcpyAsync(hinfo, dinfo, sizeof(int) * 3, cudaMemcpyDeviceToHost, s));
     SPM_CUDA_TRY(cudaStreamSynchronize(s));
     F->front.release();
     F->stack.release();
     F->work.release();
+    F->raised_pivots = hinfo[2];
     if (hinfo[0] != 0 || hinfo[1] != 0) {
         spm_set_error("zero pivot in the multifrontal factor (info %d, %d)", hinfo[0], hinfo[1]);
         return SPM_ERR_NUMERICAL;
@@ -727,20 +798,152 @@ static spm_status solve_typed(spm_problem_s *P, NDFactor *F, const void *bv, voi
     return SPM_OK;
 }
 
-spm_status spm_factor_impl(spm_problem_s *P, int prec)
+namespace {
+
+// probe right-hand side: components uniform in [-1, 1] from a splitmix64 hash of the index
+__global__ void k_probe_rhs(double2 *b128, float2 *b64, long N)
 {
-    NDFactor *&slot = prec == SPM_C128 ? P->fac128 : P->fac64;
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    uint64_t z = (uint64_t)i * 0x9E3779B97F4A7C15ull + 0x2545F4914F6CDD1Dull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    double2 v;
+    v.x = (double)(z >> 40) * (2.0 / 16777216.0) - 1.0;
+    v.y = (double)((z >> 16) & 0xFFFFFF) * (2.0 / 16777216.0) - 1.0;
+    b128[i] = v;
+    if (b64) b64[i] = make_float2((float)v.x, (float)v.y);
+}
+
+__global__ void k_widen(const float2 *a, double2 *b, long N)
+{
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) b[i] = make_double2(a[i].x, a[i].y);
+}
+
+// acc[0] += sum |y - b|^2, acc[1] += sum |b|^2
+__global__ void k_resid_norms(const double2 *y, const double2 *b, long N, double *acc)
+{
+    __shared__ double s0[256], s1[256];
+    double r = 0, q = 0;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (long)gridDim.x * blockDim.x) {
+        const double dx = y[i].x - b[i].x, dy = y[i].y - b[i].y;
+        r += dx * dx + dy * dy;
+        q += b[i].x * b[i].x + b[i].y * b[i].y;
+    }
+    s0[threadIdx.x] = r;
+    s1[threadIdx.x] = q;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) { s0[threadIdx.x] += s0[threadIdx.x + w]; s1[threadIdx.x] += s1[threadIdx.x + w]; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { atomicAdd(acc, s0[0]); atomicAdd(acc + 1, s1[0]); }
+}
+
+// ||S x - b|| / ||b|| for x = S^{-1} b through the factor of precision `prec`,
+// with b a fixed pseudo-random vector and S x formed in complex128.
+spm_status probe_factor(spm_problem_s *P, int prec, double *relres)
+{
+    const long N = 3L * P->n * P->n * P->n;
+    cudaStream_t s = P->stream;
+    DevBuf buf;
+    SPM_TRY(buf.ensure(sizeof(double2) * 3 * N + sizeof(float2) * 2 * N + 2 * sizeof(double)));
+    double2 *b = buf.as<double2>(), *x = b + N, *y = x + N;
+    float2 *b64 = reinterpret_cast<float2 *>(y + N), *x64 = b64 + N;
+    double *acc = reinterpret_cast<double *>(x64 + N);
+    const bool single = prec != SPM_C128;
+    const unsigned g = (unsigned)((N + 255) / 256);
+    k_probe_rhs<<<g, 256, 0, s>>>(b, single ? b64 : nullptr, N);
+    if (single) {
+        SPM_TRY(spm_solveS_impl(P, SPM_C64, b64, x64, 1, s));
+        k_widen<<<g, 256, 0, s>>>(x64, x, N);
+    } else {
+        SPM_TRY(spm_solveS_impl(P, SPM_C128, b, x, 1, s));
+    }
+    SPM_TRY(spm_apply_S_impl(P, SPM_C128, x, y, 1, s));
+    SPM_CUDA_TRY(cudaMemsetAsync(acc, 0, 2 * sizeof(double), s));
+    k_resid_norms<<<1024, 256, 0, s>>>(y, b, N, acc);
+    double h[2];
+    SPM_CUDA_TRY(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, s));
+    SPM_CUDA_TRY(cudaStreamSynchronize(s));
+    *relres = h[1] > 0 ? sqrt(h[0] / h[1]) : 0.0;
+    if (!(*relres == *relres)) *relres = HUGE_VAL; // NaN: an unusable factor
+    return SPM_OK;
+}
+
+// probe residual below which a factor is accepted without trying another tree
+// (measured on the n = 48 / 64 media: complex64 factors up to 3e-2 and
+// half-storage factors up to 0.3 keep GMRES within a few iterations of the
+// best tree; factors above 1 stall it)
+double probe_accept(int prec)
+{
+    return prec == SPM_C128 ? 1e-6 : (prec == SPM_C64H ? 3e-1 : 3e-2);
+}
+
+spm_status factor_once(spm_problem_s *P, int prec, int variant, NDFactor *&slot)
+{
     spm_factor_free(slot);
     slot = nullptr;
     NDFactor *F = new NDFactor();
     F->prec = prec == SPM_C128 ? SPM_C128 : SPM_C64;
-    spm_status st = prec == SPM_C128 ? factor_typed<double>(P, F, false)
-                                     : factor_typed<float>(P, F, prec == SPM_C64H);
+    spm_status st = prec == SPM_C128 ? factor_typed<double>(P, F, false, variant)
+                                     : factor_typed<float>(P, F, prec == SPM_C64H, variant);
     if (st != SPM_OK) {
         delete F;
         return st;
     }
     slot = F;
+    return SPM_OK;
+}
+
+} // namespace
+
+// Factor, probe the factor's accuracy, and if the probe residual is above the
+// acceptance level try the other tree variants, keeping the most accurate.
+spm_status spm_factor_impl(spm_problem_s *P, int prec)
+{
+    const int fi = prec == SPM_C128 ? 0 : 1;
+    NDFactor *&slot = fi == 0 ? P->fac128 : P->fac64;
+    int best_v = -1, attempts = 0;
+    double best = HUGE_VAL, last = HUGE_VAL;
+    for (int v = 0; v < TREE_VARIANTS; ++v) {
+        SPM_TRY(factor_once(P, prec, v, slot));
+        ++attempts;
+        SPM_TRY(probe_factor(P, prec, &last));
+        if (last < best) { best = last; best_v = v; }
+        if (last <= probe_accept(prec)) break;
+    }
+    if (best_v != slot->variant) { // a later variant was worse: rebuild the best one
+        SPM_TRY(factor_once(P, prec, best_v, slot));
+        ++attempts;
+    }
+    P->fac_info[fi].variant = best_v;
+    P->fac_info[fi].attempts = attempts;
+    P->fac_info[fi].raised_pivots = slot->raised_pivots;
+    P->fac_info[fi].probe_relres = best;
+    P->fac_info[fi].half_store = prec == SPM_C64H;
+    return SPM_OK;
+}
+
+// Factor on one given tree variant (no retry); the probe is still recorded.
+spm_status spm_factor_tree_impl(spm_problem_s *P, int prec, int variant)
+{
+    if (variant < 0 || variant >= TREE_VARIANTS) {
+        spm_set_error("tree variant must be in [0, %d)", TREE_VARIANTS);
+        return SPM_ERR_INVALID_ARG;
+    }
+    const int fi = prec == SPM_C128 ? 0 : 1;
+    NDFactor *&slot = fi == 0 ? P->fac128 : P->fac64;
+    SPM_TRY(factor_once(P, prec, variant, slot));
+    double r = 0;
+    SPM_TRY(probe_factor(P, prec, &r));
+    P->fac_info[fi].variant = variant;
+    P->fac_info[fi].attempts = 1;
+    P->fac_info[fi].raised_pivots = slot->raised_pivots;
+    P->fac_info[fi].probe_relres = r;
+    P->fac_info[fi].half_store = prec == SPM_C64H;
     return SPM_OK;
 }
 

@@ -201,3 +201,36 @@ def test_apply_A_full_size_n128_c64(spm):
     e = rel(got - x, ref - x)
     print(f"n=128 c64: rel err of (A-I)x = {e:.2e}")
     assert e < 2e-5
+
+
+@pytest.mark.parametrize("n", [16, 32, 48, 64])
+def test_every_zpass_kernel_matches_oracle(spm, n):
+    """Each z-pass kernel (four lines in registers, one field at a time after a
+    cp.async prefetch, persistent TMA-fed) gives the same apply: complex128 to
+    1e-12 and complex64 to 2e-5 of the FP64 oracle, for one and three
+    right-hand sides; no bounded device wait gives up."""
+    L = 2 * n
+    variants = [spm.ZPASS_ONE, spm.ZPASS_TMA] if L in (96, 192) else \
+        ([spm.ZPASS_FOUR, spm.ZPASS_ONE, spm.ZPASS_TMA] if L >= 32 else [spm.ZPASS_FOUR])
+    P, k, m, p = make(spm, n, "bumps", seed=n)
+    for nrhs in (1, 3):
+        x = si.random_field(n, 300 + n, nrhs)
+        ref = oracle.apply_fft(n, k, m, p, x)
+        for prec, dtype, tol in ((spm.SPM_C128, torch.complex128, 1e-12), (spm.SPM_C64, torch.complex64, 2e-5)):
+            saved = spm.get_apply_plan(prec, L)
+            try:
+                for z in variants:
+                    spm.set_apply_plan(prec, L, z)
+                    y = torch.zeros(x.shape, dtype=dtype, device="cuda")
+                    P.apply_A(to_dev(x, dtype), y)
+                    P.device_status()
+                    e = rel(y.cpu().numpy().astype(np.complex128), ref)
+                    print(f"n={n} nrhs={nrhs} prec={prec} z-pass {z}: rel err {e:.2e}")
+                    assert e < tol, (z, e)
+                    assert spm.get_apply_plan(prec, L) == z
+            finally:
+                spm.set_apply_plan(prec, L, saved)
+    with pytest.raises(spm.SpmError):
+        spm.set_apply_plan(spm.SPM_C64, 96, spm.ZPASS_FOUR)
+    with pytest.raises(spm.SpmError):
+        spm.set_apply_plan(spm.SPM_C64, 100, spm.ZPASS_ONE)

@@ -214,3 +214,36 @@ def test_half_storage_factor(spm):
     print(f"n=64 mixed, half-storage factor: iterations {info.iterations}, relres {info.true_relres:.2e}")
     assert info.true_relres <= 1e-6
     assert info.iterations <= 16
+
+
+def test_tree_variants_and_factor_probe(spm):
+    """Every nested-dissection tree variant (cut planes moved by one) factors S
+    exactly: S^-1 b matches the oracle's banded LU, and the recorded probe
+    residual ||S x - b|| / ||b|| is at the precision's rounding level."""
+    n = 16
+    k = si.wavenumber_for_grid(n)
+    eps, grad = si.medium_bumps(n, seed=3, count=8)
+    P = spm.Problem(n, k, eps, grad)
+    al, be, _ = oracle.all_stencils(n, k)
+    P.set_stencils(al, be)
+    m, p = oracle.medium(eps, grad)
+    b = si.random_field(n, 23)
+    ref = oracle.SFactor(n, m, p, al, be).solve(b)
+    for v in range(4):
+        P.factor_S_tree(spm.SPM_C128, v)
+        x = torch.zeros(b.shape, dtype=torch.complex128, device="cuda")
+        P.solve_S(dev(b), x)
+        torch.cuda.synchronize()
+        e = rel(x.cpu().numpy(), ref)
+        variant, attempts, half, probe, raised = P.factor_info(spm.SPM_C128)
+        print(f"variant {v}: S^-1 rel err {e:.2e}, probe {probe:.2e}")
+        assert (variant, attempts, half, raised) == (v, 1, False, 0)
+        assert e < 1e-9 and probe < 1e-10
+        P.factor_S_tree(spm.SPM_C64, v)
+        assert P.factor_info(spm.SPM_C64)[3] < 1e-3
+    with pytest.raises(spm.SpmError):
+        P.factor_S_tree(spm.SPM_C128, 4)
+    # the retrying factor accepts the first tree here and reports it
+    P.factor_S(spm.SPM_C64)
+    variant, attempts, half, probe, raised = P.factor_info(spm.SPM_C64)
+    assert (variant, attempts, half, raised) == (0, 1, False, 0) and probe <= 1e-2
