@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--solve", default="mixed", choices=["none", "mixed", "both"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--uneven-solve-all", action="store_true",
+                    help="uneven32: also solve the n = 96 problems, one after another")
     return ap.parse_args()
 
 
@@ -165,10 +167,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(wl, seconds, op):
-    """FP64 oracle apply (A, then Q for op QA) on a bounded sample: whole applies
-    until about `seconds` have passed.  For Q the stencil tables are seeded
-    random numbers: the oracle's cost does not depend on their values."""
+def cpu_baseline(wl, seconds, op, max_steps=None, warmup=1):
+    """FP64 oracle apply (A, then Q for op QA) on a bounded sample: `warmup`
+    untimed applies, then whole timed applies until about `seconds` have passed
+    (or `max_steps` applies).  For Q the stencil tables are seeded random
+    numbers: the oracle's cost does not depend on their values."""
     import oracle
     n, k = wl["n"], wl["omega"]
     m, p = oracle.medium(wl["eps"], wl["grad"])
@@ -182,10 +185,11 @@ def cpu_baseline(wl, seconds, op):
             y = oracle.apply_Q(n, alpha, y)
         return y
 
-    one()  # warm
+    for _ in range(max(1, warmup)):
+        one()
     t0 = time.perf_counter()
     count = 0
-    while True:
+    while max_steps is None or count < max_steps:
         one()
         count += 1
         if time.perf_counter() - t0 > seconds:
@@ -194,22 +198,27 @@ def cpu_baseline(wl, seconds, op):
     F.close()
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     what = "A then Q" if op == "QA" else "A"
-    return {"value": count / dt, "unit": "applies/s", "cores": cores, "kind": "oracle",
+    return {"value": count / dt, "unit": "applies/s", "cores": cores, "kind": "oracle", "steps_run": count,
             "sample": f"{count} FP64 oracle applies of {what} at n={n} (kernel spectra precomputed), "
                       f"{dt:.1f} s on {cores} host threads"}
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle as it stands.  One step is one whole
+    oracle apply; the run stops after --steps steps or --cpu-seconds of timed
+    work, whichever comes first (a full oracle apply at n = 64 takes about
+    0.2 s on 16 host threads), and reports the steps it ran."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     wl = si.workload(args.workload)
-    cb = cpu_baseline(wl, args.cpu_seconds, args.op)
+    cb = cpu_baseline(wl, args.cpu_seconds, args.op, max_steps=args.steps, warmup=min(args.warmup, 3))
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "applies/s",
-            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "n_gpus": args.gpus, "steps": cb["steps_run"], "steps_requested": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 / cb["value"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-            "config": {"workload": args.workload, "n": wl["n"], "nrhs": 1, "op": args.op},
+            "config": {"workload": args.workload, "n": wl["n"], "nrhs": 1, "op": args.op,
+                       "parallelism": "replicas1"},
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": "applies/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -340,8 +349,40 @@ def run_uneven(args, torch, spm, rank, world, local):
                          "mixed_half_factor_batch_time_s": time.perf_counter() - t0, "status": st,
                          "max_iterations": max(i.iterations for i in infos),
                          "max_true_relres": max(i.true_relres for i in infos),
-                         "setup_stencils_factor_c64_half_storage_s": setup_s,
-                         "excluded": "n = 96 problems: apply only (factor memory)"}
+                         "setup_stencils_factor_c64_half_storage_s": setup_s}
+        big = [q for q in probs if q["n"] > 64]
+        if args.uneven_solve_all and big:
+            # the n = 96 problems one after another: set-up, solve, release
+            B2.close()
+            del B2, gs, xs2
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
+            rows = []
+            for q in big:
+                Pq = spm.Problem(q["n"], q["omega"], q["eps"], q["grad"])
+                t0 = time.perf_counter()
+                Pq.build_stencils(spm.SPM_C64H)
+                torch.cuda.synchronize()
+                su = time.perf_counter() - t0
+                e = torch.from_numpy(q["einc"]).to("cuda")
+                g = torch.zeros_like(e)
+                Pq.rhs_from_incident(e, g)
+                xq = torch.zeros_like(g)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                info, stq = Pq.solve(g, xq, prec=spm.SPM_MIXED, tol=1e-6, maxit=400, check=False)
+                torch.cuda.synchronize()
+                variant, attempts, _, probe, _ = Pq.factor_info(spm.SPM_C64)
+                rows.append({"setup_s": su, "solve_s": time.perf_counter() - t0, "iterations": info.iterations,
+                             "true_relres": info.true_relres, "status": stq, "tree_variant": variant,
+                             "factorisations": attempts, "probe": probe})
+                Pq.close()
+                del Pq, e, g, xq
+                torch.cuda.empty_cache()
+            line["solve"]["n96_one_at_a_time"] = rows
+        elif big:
+            line["solve"]["excluded"] = ("n = 96 problems: apply only here (factor 65-131 GB each; "
+                                         "--uneven-solve-all solves them one after another)")
     if rank == 0:
         print(json.dumps(line), flush=True)
 

@@ -169,6 +169,13 @@ spm_status spm_factor_S(spm_problem prob, spm_prec prec);
  * SPM_ERR_INVALID_ARG for a variant outside [0, 4). */
 spm_status spm_factor_S_tree(spm_problem prob, spm_prec prec, int variant);
 
+/* Process-wide GEMM mode of the complex64 factors built afterwards: 0 (the
+ * default) runs the Schur-complement updates in FP32 on the CUDA cores, 1 lets
+ * cuBLAS emulate FP32 on the BF16 tensor cores (BF16x9, FP32-level accuracy).
+ * The probe of spm_factor_S checks either.  SPM_ERR_INVALID_ARG otherwise. */
+spm_status spm_set_factor_gemm(int mode);
+spm_status spm_get_factor_gemm(int *mode);
+
 /* Report on the current factor in `prec` (SPM_C128, or SPM_C64 / SPM_C64H for
  * the complex64 slot): tree variant kept (0 = middle cuts), factorisations run
  * by the last spm_factor_S, whether blocks are in half storage, the number of
@@ -209,6 +216,12 @@ spm_status spm_set_apply_plan(spm_prec prec, int L, int zvariant);
  * TMA-fed z-pass waits on its copies with an iteration limit instead of
  * spinning forever, and leaves its output incomplete when the limit is hit. */
 spm_status spm_device_status(spm_problem prob);
+
+/* Self-test of that failure path: launches (on the problem's stream) one block
+ * that waits, with the same bound, on an mbarrier no copy will complete, and
+ * records the expired wait like the z-pass does; the next spm_device_status
+ * then returns SPM_ERR_TIMEOUT.  Takes about as long as one bounded wait. */
+spm_status spm_selftest_bounded_wait(spm_problem prob);
 
 /* ------------------------------------------------------------- solving */
 

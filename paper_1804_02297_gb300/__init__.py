@@ -23,7 +23,7 @@ SPM_C128, SPM_C64, SPM_MIXED, SPM_C64H = 0, 1, 2, 3
 # every symbol include/spm.h declares
 EXPORTS = [
     "spm_create_problem", "spm_destroy", "spm_problem_info", "spm_apply_A", "spm_apply_QA", "spm_apply_Q",
-    "spm_build_stencils", "spm_set_stencils", "spm_get_stencils", "spm_factor_S", "spm_factor_S_tree", "spm_factor_info", "spm_device_status", "spm_get_apply_plan", "spm_set_apply_plan", "spm_apply_S",
+    "spm_build_stencils", "spm_set_stencils", "spm_get_stencils", "spm_factor_S", "spm_factor_S_tree", "spm_factor_info", "spm_device_status", "spm_selftest_bounded_wait", "spm_set_factor_gemm", "spm_get_factor_gemm", "spm_get_apply_plan", "spm_set_apply_plan", "spm_apply_S",
     "spm_solve_S", "spm_incident_plane_wave", "spm_rhs_from_incident", "spm_solve", "spm_kernel_entries",
     "spm_lattice_constant", "spm_last_error", "spm_apply_A_noalloc",
     "spm_create_batch", "spm_destroy_batch", "spm_batch_size", "spm_batch_problem", "spm_batch_build_stencils",
@@ -39,6 +39,17 @@ def get_apply_plan(prec, L):
     z = ctypes.c_int()
     _check(lib.spm_get_apply_plan(prec, L, ctypes.byref(z)))
     return z.value
+
+
+def set_factor_gemm(mode):
+    """GEMM mode of complex64 factors built afterwards: 0 FP32, 1 BF16x9-emulated FP32."""
+    _check(lib.spm_set_factor_gemm(int(mode)))
+
+
+def get_factor_gemm():
+    m = ctypes.c_int()
+    _check(lib.spm_get_factor_gemm(ctypes.byref(m)))
+    return m.value
 
 
 def set_apply_plan(prec, L, zvariant):
@@ -82,6 +93,9 @@ def _load():
         "spm_factor_info": [P, I, ctypes.POINTER(FactorReport)],
         "spm_factor_S_tree": [P, I, I],
         "spm_device_status": [P],
+        "spm_selftest_bounded_wait": [P],
+        "spm_set_factor_gemm": [I],
+        "spm_get_factor_gemm": [ctypes.POINTER(I)],
         "spm_get_apply_plan": [I, I, ctypes.POINTER(I)],
         "spm_set_apply_plan": [I, I, I],
         "spm_apply_S": [P, I, P, P, I, P],
@@ -190,6 +204,10 @@ class Problem:
         n, k, u = ctypes.c_int(), ctypes.c_double(), ctypes.c_longlong()
         _check(lib.spm_problem_info(self.h, ctypes.byref(n), ctypes.byref(k), ctypes.byref(u)))
         return n.value, k.value, u.value
+
+    def selftest_bounded_wait(self):
+        """Launch a block whose bounded wait must expire (see spm_selftest_bounded_wait)."""
+        _check(lib.spm_selftest_bounded_wait(self.h))
 
     def device_status(self):
         """Synchronise; raise SpmError(SPM_ERR_TIMEOUT) if a bounded device wait gave up."""

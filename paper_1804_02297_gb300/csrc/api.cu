@@ -327,6 +327,26 @@ extern "C" spm_status spm_set_apply_plan(spm_prec prec, int L, int zvariant)
     return spm_apply_plan_impl(prec, L, nullptr, &zvariant);
 }
 
+extern "C" spm_status spm_set_factor_gemm(int mode)
+{
+    if (mode != 0 && mode != 1) { spm_set_error("factor GEMM mode must be 0 (FP32) or 1 (BF16x9-emulated FP32)"); return SPM_ERR_INVALID_ARG; }
+    spm_set_factor_gemm_mode(mode);
+    return SPM_OK;
+}
+
+extern "C" spm_status spm_get_factor_gemm(int *mode)
+{
+    if (!mode) { spm_set_error("NULL argument"); return SPM_ERR_INVALID_ARG; }
+    *mode = spm_factor_gemm_mode();
+    return SPM_OK;
+}
+
+extern "C" spm_status spm_selftest_bounded_wait(spm_problem P)
+{
+    if (!P) { spm_set_error("NULL problem"); return SPM_ERR_INVALID_ARG; }
+    return spm_wait_selftest_impl(P);
+}
+
 extern "C" spm_status spm_device_status(spm_problem P)
 {
     if (!P) { spm_set_error("NULL problem"); return SPM_ERR_INVALID_ARG; }

@@ -18,6 +18,7 @@
 
 #include <atomic>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "fft.cuh"
@@ -187,6 +188,41 @@ __global__ void __launch_bounds__(tx_of<R, L>::v * L / line_elems(L)) k2_cols(co
         if (t + T * q < nout) dst[(long)(t + T * q) * inner] = v[q];
 }
 
+// Same strided lines, two z planes per block (E = 8 lengths): both planes'
+// columns are loaded before either is transformed, and the two transforms share
+// every barrier (fft_lines), so each thread keeps twice the loads in flight.
+template <typename R, int L, int DIR, bool PRUNE>
+__global__ void __launch_bounds__(tx_of<R, L>::v * L / 8) k2_cols2(const typename cplx_of<R>::type *in, typename cplx_of<R>::type *out,
+                                                                 int nout, long inner, int F, long ib, long if_, long iz, long ob,
+                                                                 long of, long oz, const typename cplx_of<R>::type *__restrict__ tw)
+{
+    using C = typename cplx_of<R>::type;
+    constexpr int T = L / 8, TX = tx_of<R, L>::v;
+    extern __shared__ unsigned char smem_raw[];
+    C *sm = reinterpret_cast<C *>(smem_raw); // [2][L][TX]
+    const int c = threadIdx.x % TX, t = threadIdx.x / TX;
+    const long i0 = (long)blockIdx.x * TX;
+    const int z0 = 2 * blockIdx.y;
+    const int b = blockIdx.z / F, f = blockIdx.z % F;
+    C v[2][8];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const C *src = in + b * ib + f * if_ + (z0 + k) * iz + i0 + c;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[k][q] = (!PRUNE || q < 4) ? src[(long)(t + T * q) * inner] : czero<C>();
+    }
+    auto buf = [&](int k, int pos) -> C & { return sm[(k * L + pos) * TX + c]; };
+    auto sync = [&]() { __syncthreads(); };
+    fftr::fft_lines<DIR, L, PRUNE, 2>(v, t, buf, sync, tw);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        C *dst = out + b * ob + f * of + (z0 + k) * oz + i0 + c;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (t + T * q < nout) dst[(long)(t + T * q) * inner] = v[k][q];
+    }
+}
+
 // zprod: lines along z of W2[b][4][z<n][eta][xi] (TX adjacent columns), product
 // with the octant spectra, inverse along z, keep z < n (in place, fields 0..2).
 // The four fields' columns are prefetched into shared memory with cp.async at
@@ -330,13 +366,13 @@ __global__ void __launch_bounds__(256) k2_xinv(const typename cplx_of<R>::type *
     C *lb = sm + line * LS;
     auto buf = [&](int pos) -> C & { return lb[xpad<L>(pos)]; };
     auto sync = [&]() { if (T <= 32) __syncwarp(); else __syncthreads(); };
+    C xi[H]; // the identity term, loaded before the transform so its latency overlaps it
+#pragma unroll
+    for (int q = 0; q < H; ++q) xi[q] = ok ? xin[g * n + t + T * q] : czero<C>();
     line_fft<1, L, false>(v, t, buf, sync, tw);
     if (ok) {
 #pragma unroll
-        for (int q = 0; q < H; ++q) {
-            long o = g * n + t + T * q;
-            y[o] = xin[o] + v[q];
-        }
+        for (int q = 0; q < H; ++q) y[g * n + t + T * q] = xi[q] + v[q];
     }
 }
 
@@ -382,6 +418,22 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
                      smem_u32(dst)),
                  "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
                  : "memory");
+}
+
+// Self-test of the bounded wait: an mbarrier expecting 16 bytes that no copy
+// delivers; every thread waits with the same bound as the TMA z-pass, and the
+// expired wait is recorded in *err (code 2) exactly as the z-pass records one.
+__global__ void k_wait_selftest(int *err)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+        mbar_expect_tx(&bar, 16);
+    }
+    __syncthreads();
+    const bool ok = mbar_wait(&bar, 0);
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicExch(err, 2);
 }
 
 // zpass fed by TMA: a persistent grid walks the tiles (TX adjacent columns of
@@ -569,6 +621,10 @@ spm_status apply_chunk_v2(const typename cplx_of<R>::type *xb, typename cplx_of<
         allow_smem(k2_xinv<R, L>, sm_rows);
         allow_smem(k2_cols<R, L, -1, true>, sm_cols);
         allow_smem(k2_cols<R, L, 1, false>, sm_cols);
+        if constexpr (line_elems(L) == 8) {
+            allow_smem(k2_cols2<R, L, -1, true>, 2 * sm_cols);
+            allow_smem(k2_cols2<R, L, 1, false>, 2 * sm_cols);
+        }
         if constexpr (line_elems(L) == 8) allow_smem(k2_zprod4<R, L>, sm_zprod4);
         allow_smem(k2_zprod1<R, L>, sm_zprod);
         attrs = true;
@@ -579,8 +635,12 @@ spm_status apply_chunk_v2(const typename cplx_of<R>::type *xb, typename cplx_of<
         long rows = (long)nb * n2;
         k2_xfwd<R, L><<<(unsigned)((rows + LPB - 1) / LPB), LPB * T, sm_rows, s>>>(xb, m, p, W1, (int)rows, tw);
     }
-    k2_cols<R, L, -1, true><<<dim3(L / TX, n, nb * 4), THR, sm_cols, s>>>(
-        W1, W2, L, L, 4, 4 * n2 * L, n2 * L, n * (long)L, 4 * (long)n * L2, (long)n * L2, L2, tw);
+    if constexpr (line_elems(L) == 8 && n % 2 == 0)
+        k2_cols2<R, L, -1, true><<<dim3(L / TX, n / 2, nb * 4), THR, 2 * sm_cols, s>>>(
+            W1, W2, L, L, 4, 4 * n2 * L, n2 * L, n * (long)L, 4 * (long)n * L2, (long)n * L2, L2, tw);
+    else
+        k2_cols<R, L, -1, true><<<dim3(L / TX, n, nb * 4), THR, sm_cols, s>>>(
+            W1, W2, L, L, 4, 4 * n2 * L, n2 * L, n * (long)L, 4 * (long)n * L2, (long)n * L2, L2, tw);
     bool done = false;
     if constexpr (L >= 32) {
         if (zvar == ZPROD_TMA) {
@@ -595,8 +655,12 @@ spm_status apply_chunk_v2(const typename cplx_of<R>::type *xb, typename cplx_of<
         }
     }
     if (!done) k2_zprod1<R, L><<<dim3((unsigned)(L2 / TX), nb), THR, sm_zprod, s>>>(W2, spec, tw);
-    k2_cols<R, L, 1, false><<<dim3(L / TX, n, nb * 3), THR, sm_cols, s>>>(
-        W2, W1, n, L, 3, 4 * (long)n * L2, (long)n * L2, L2, 3 * n2 * L, n2 * L, n * (long)L, tw);
+    if constexpr (line_elems(L) == 8 && n % 2 == 0)
+        k2_cols2<R, L, 1, false><<<dim3(L / TX, n / 2, nb * 3), THR, 2 * sm_cols, s>>>(
+            W2, W1, n, L, 3, 4 * (long)n * L2, (long)n * L2, L2, 3 * n2 * L, n2 * L, n * (long)L, tw);
+    else
+        k2_cols<R, L, 1, false><<<dim3(L / TX, n, nb * 3), THR, sm_cols, s>>>(
+            W2, W1, n, L, 3, 4 * (long)n * L2, (long)n * L2, L2, 3 * n2 * L, n2 * L, n * (long)L, tw);
     {
         long rows = (long)nb * 3 * n2;
         k2_xinv<R, L><<<(unsigned)((rows + LPB - 1) / LPB), LPB * T, sm_rows, s>>>(W1, xb, yb, rows, tw);
@@ -758,6 +822,13 @@ static_assert(QX * QY * QZ == Q_THREADS && QF_U * QF_W == Q_THREADS, "Q block sh
 template <typename C> struct QInterior {
     C a[243]; // [d][o][c], o = (o3+1)*9 + (o2+1)*3 + (o1+1)
 };
+// complex64: each coefficient a as the packed pairs (a.x, a.x, -a.y, a.y), so a
+// complex MAC acc += a v is two packed FP32x2 FMAs, (a.x, a.x) (v.x, v.y) and
+// (-a.y, a.y) (v.y, v.x)
+template <> struct QInterior<float2> {
+    float4 a[243];
+};
+static_assert(sizeof(QInterior<float2>) + 64 <= 4096, "kernel parameter space");
 
 // edge point number e (0 <= e < 12 (n-2) + 8) -> (i1, i2, i3): corners, then the
 // edges along x, y, z (four each)
@@ -808,10 +879,19 @@ __device__ __forceinline__ void q_interior_block(int blk, const C *__restrict__ 
 #pragma unroll
                 for (int o1 = -1; o1 <= 1; ++o1, ++o) {
                     const int h = ((lz + 1 + o3) * QHY + (ly + 1 + o2)) * QHX + (lx + 1 + o1);
-                    const C val = sv[d * QH + h];
-                    acc0 = cfma(qa.a[(d * 27 + o) * 3 + 0], val, acc0);
-                    acc1 = cfma(qa.a[(d * 27 + o) * 3 + 1], val, acc1);
-                    acc2 = cfma(qa.a[(d * 27 + o) * 3 + 2], val, acc2);
+                    if constexpr (std::is_same<C, float2>::value) {
+                        const float2 vv = sv[d * QH + h], vs = make_float2(vv.y, vv.x);
+                        const float4 a0 = qa.a[(d * 27 + o) * 3 + 0], a1 = qa.a[(d * 27 + o) * 3 + 1],
+                                     a2 = qa.a[(d * 27 + o) * 3 + 2];
+                        acc0 = __ffma2_rn(make_float2(a0.z, a0.w), vs, __ffma2_rn(make_float2(a0.x, a0.y), vv, acc0));
+                        acc1 = __ffma2_rn(make_float2(a1.z, a1.w), vs, __ffma2_rn(make_float2(a1.x, a1.y), vv, acc1));
+                        acc2 = __ffma2_rn(make_float2(a2.z, a2.w), vs, __ffma2_rn(make_float2(a2.x, a2.y), vv, acc2));
+                    } else {
+                        const C val = sv[d * QH + h];
+                        acc0 = cfma(qa.a[(d * 27 + o) * 3 + 0], val, acc0);
+                        acc1 = cfma(qa.a[(d * 27 + o) * 3 + 1], val, acc1);
+                        acc2 = cfma(qa.a[(d * 27 + o) * 3 + 2], val, acc2);
+                    }
                 }
     }
     const long i = ((long)i3 * n + i2) * n + i1;
@@ -955,8 +1035,9 @@ spm_status apply_Q_typed(spm_problem_s *P, const void *vv, void *yv, int nrhs, c
     // interior coefficients (class 13) by value, from the host copy of the table
     QInterior<C> qa;
     for (int i = 0; i < 243; ++i) {
-        qa.a[i].x = (R)P->qtab_h[2 * (13 * 243 + i)];
-        qa.a[i].y = (R)P->qtab_h[2 * (13 * 243 + i) + 1];
+        const R ax = (R)P->qtab_h[2 * (13 * 243 + i)], ay = (R)P->qtab_h[2 * (13 * 243 + i) + 1];
+        if constexpr (sizeof(R) == 4) qa.a[i] = make_float4(ax, ax, -ay, ay);
+        else { qa.a[i].x = ax; qa.a[i].y = ay; }
     }
     const C *v = reinterpret_cast<const C *>(vv);
     C *y = reinterpret_cast<C *>(yv);
@@ -1013,6 +1094,13 @@ static int zplan_supported(int L)
 {
     const bool e8 = !(L == 96 || L == 192);
     return (e8 ? 1 << ZPROD_FOUR : 0) | ((!e8 || L >= 32) ? 1 << ZPROD_ONE : 0) | (L >= 32 ? 1 << ZPROD_TMA : 0);
+}
+
+spm_status spm_wait_selftest_impl(spm_problem_s *P)
+{
+    k_wait_selftest<<<1, 32, 0, P->stream>>>(P->dev_err.as<int>());
+    SPM_CUDA_TRY(cudaGetLastError());
+    return SPM_OK;
 }
 
 spm_status spm_apply_plan_impl(int prec, int L, int *get, const int *set)

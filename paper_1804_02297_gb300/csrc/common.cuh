@@ -150,6 +150,7 @@ struct spm_problem_s {
 spm_status spm_apply_A_impl(spm_problem_s *P, int prec, const void *x, void *y, int nrhs, cudaStream_t s);
 spm_status spm_apply_Q_impl(spm_problem_s *P, int prec, const void *v, void *y, int nrhs, cudaStream_t s);
 spm_status spm_apply_plan_impl(int prec, int L, int *get, const int *set);
+spm_status spm_wait_selftest_impl(spm_problem_s *P);
 spm_status spm_build_qtable(spm_problem_s *P);
 spm_status spm_build_spectra(spm_problem_s *P);
 spm_status spm_stencils_device(spm_problem_s *P);
@@ -159,5 +160,7 @@ spm_status spm_factor_impl(spm_problem_s *P, int prec);
 spm_status spm_factor_tree_impl(spm_problem_s *P, int prec, int variant);
 spm_status spm_solveS_impl(spm_problem_s *P, int prec, const void *b, void *x, int nrhs, cudaStream_t s);
 void spm_factor_free(NDFactor *f);
+int spm_factor_gemm_mode();
+void spm_set_factor_gemm_mode(int m);
 spm_status spm_solve_impl(spm_problem_s *P, int prec, const void *g, void *x, int nrhs, double tol,
                           int maxit, int restart, spm_solve_info *info);

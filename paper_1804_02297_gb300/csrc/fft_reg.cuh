@@ -24,6 +24,10 @@ __host__ __device__ constexpr int span_of(int L, int s) { return s == 0 ? 1 : ra
 
 template <typename C> __device__ __forceinline__ C add(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
 template <typename C> __device__ __forceinline__ C sub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+// complex64: one packed FP32x2 instruction per complex add or subtract
+// (a - b = fma(b, -1, a), exact like the subtraction)
+__device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
 
 // multiply by exp(DIR i pi/4)^e for e = 1, 2, 3
 template <int DIR, int E, typename C> __device__ __forceinline__ C w8(C a)

@@ -29,6 +29,7 @@
 #include <cusolverDn.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <type_traits>
 #include <vector>
@@ -411,6 +412,12 @@ struct NDFactor {
 void spm_factor_free(NDFactor *f) { delete f; }
 
 namespace {
+std::atomic<int> g_factor_gemm(0);
+}
+int spm_factor_gemm_mode() { return g_factor_gemm.load(); }
+void spm_set_factor_gemm_mode(int m) { g_factor_gemm.store(m); }
+
+namespace {
 
 constexpr int LEAF_SIDE = 5;
 
@@ -575,6 +582,10 @@ static spm_status factor_typed(spm_problem_s *P, NDFactor *F, bool half_store, i
     if (!F->cusolver && cusolverDnCreate(&F->cusolver) != CUSOLVER_STATUS_SUCCESS) { spm_set_error("cusolverDnCreate failed"); return SPM_ERR_CUDA; }
     cublasSetStream(F->cublas, s);
     cusolverDnSetStream(F->cusolver, s);
+    // complex64 factors: the Schur-complement GEMMs in plain FP32, or FP32
+    // emulated on the BF16 tensor cores (BF16x9, FP32-level accuracy) when chosen
+    cublasSetMathMode(F->cublas, (sizeof(R) == 4 && spm_factor_gemm_mode() == 1) ? CUBLAS_FP32_EMULATED_BF16X9_MATH
+                                                                               : CUBLAS_DEFAULT_MATH);
     int lwork = 0;
     if (BT::getrf_ws(F->cusolver, (int)F->max_own3, F->front.as<C>(), (int)max_f, &lwork) != CUSOLVER_STATUS_SUCCESS) {
         spm_set_error("getrf buffer size query failed");

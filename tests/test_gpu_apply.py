@@ -234,3 +234,29 @@ def test_every_zpass_kernel_matches_oracle(spm, n):
         spm.set_apply_plan(spm.SPM_C64, 96, spm.ZPASS_FOUR)
     with pytest.raises(spm.SpmError):
         spm.set_apply_plan(spm.SPM_C64, 100, spm.ZPASS_ONE)
+
+
+@pytest.mark.parametrize("n", [16, 48])
+def test_apply_Q_ragged_tiles_random_stencils(spm, n):
+    """Q alone (Eq. nbr_i_block_alpha) with seeded random stencil tables, at sizes
+    whose interior (32x4x2) and face (32x8) tiles end ragged: complex128 to
+    1e-14 and complex64 to 5e-6 of the oracle's gather (243 FP32 products per
+    output, unit roundoff 6e-8 times about sqrt(243)), two right-hand sides."""
+    P, k, m, p = make(spm, n, "bumps", seed=n)
+    rng = np.random.default_rng(n)
+    al = rng.standard_normal((27, 81, 3)) + 1j * rng.standard_normal((27, 81, 3))
+    be = rng.standard_normal((27, 108, 3)) + 1j * rng.standard_normal((27, 108, 3))
+    P.set_stencils(al, be)
+    v = si.random_field(n, 41 + n, 2)
+    ref = oracle.apply_Q(n, al, v)
+    y = torch.zeros(v.shape, dtype=torch.complex128, device="cuda")
+    P.apply_Q(to_dev(v), y)
+    torch.cuda.synchronize()
+    e128 = rel(y.cpu().numpy(), ref)
+    y64 = torch.zeros(v.shape, dtype=torch.complex64, device="cuda")
+    P.apply_Q(to_dev(v, torch.complex64), y64)
+    torch.cuda.synchronize()
+    e64 = rel(y64.cpu().numpy().astype(np.complex128), ref)
+    print(f"n={n}: Q c128 {e128:.2e}, c64 {e64:.2e}")
+    assert e128 < 1e-14
+    assert e64 < 5e-6

@@ -247,3 +247,26 @@ def test_tree_variants_and_factor_probe(spm):
     P.factor_S(spm.SPM_C64)
     variant, attempts, half, probe, raised = P.factor_info(spm.SPM_C64)
     assert (variant, attempts, half, raised) == (0, 1, False, 0) and probe <= 1e-2
+
+
+def test_nearly_singular_box_is_avoided_by_tree_retry(spm):
+    """Problem 17 of the uneven batch (n = 48, 8 bumps): the middle-cut dissection
+    tree contains a nearly singular box, so its complex64 factor is unusable
+    (probe residual above 1, GMRES stalls); spm_factor_S detects this with its
+    probe, keeps a shifted tree, and the mixed solve then reaches 1e-6 quickly."""
+    q = si.uneven_batch(32)[17]
+    n = q["n"]
+    P = spm.Problem(n, q["omega"], q["eps"], q["grad"])
+    P.build_stencils(spm.SPM_C64)
+    variant, attempts, half, probe, _ = P.factor_info(spm.SPM_C64)
+    print(f"kept tree variant {variant} after {attempts} factorisations, probe {probe:.2e}")
+    assert variant != 0 and attempts >= 2 and probe <= 3e-2
+    e = dev(q["einc"])
+    g = torch.zeros_like(e)
+    P.rhs_from_incident(e, g)
+    x = torch.zeros_like(g)
+    info, _ = P.solve(g, x, prec=spm.SPM_MIXED, tol=1e-6, maxit=200)
+    print(f"mixed solve: {info.iterations} iterations, relres {info.true_relres:.2e}")
+    assert info.true_relres <= 1e-6 and info.iterations <= 15
+    P.factor_S_tree(spm.SPM_C64, 0)
+    assert P.factor_info(spm.SPM_C64)[3] > 1.0  # the middle-cut tree really is the bad one
