@@ -357,11 +357,20 @@ def run_uneven(args, torch, spm, rank, world, local):
             del B2, gs, xs2
             torch.cuda.synchronize()
             torch.cuda.empty_cache()
+            line["solve"]["free_gb_after_batch_release"] = torch.cuda.mem_get_info()[0] / 1e9
             rows = []
             for q in big:
+                free_gb = torch.cuda.mem_get_info()[0] / 1e9
                 Pq = spm.Problem(q["n"], q["omega"], q["eps"], q["grad"])
                 t0 = time.perf_counter()
-                Pq.build_stencils(spm.SPM_C64H)
+                try:
+                    Pq.build_stencils(spm.SPM_C64H)
+                except spm.SpmError as err:
+                    rows.append({"status": err.status, "error": str(err), "free_gb_before": free_gb})
+                    Pq.close()
+                    del Pq
+                    torch.cuda.empty_cache()
+                    continue
                 torch.cuda.synchronize()
                 su = time.perf_counter() - t0
                 e = torch.from_numpy(q["einc"]).to("cuda")
@@ -373,7 +382,8 @@ def run_uneven(args, torch, spm, rank, world, local):
                 info, stq = Pq.solve(g, xq, prec=spm.SPM_MIXED, tol=1e-6, maxit=400, check=False)
                 torch.cuda.synchronize()
                 variant, attempts, _, probe, _ = Pq.factor_info(spm.SPM_C64)
-                rows.append({"setup_s": su, "solve_s": time.perf_counter() - t0, "iterations": info.iterations,
+                rows.append({"free_gb_before": free_gb, "setup_s": su, "solve_s": time.perf_counter() - t0,
+                             "iterations": info.iterations,
                              "true_relres": info.true_relres, "status": stq, "tree_variant": variant,
                              "factorisations": attempts, "probe": probe})
                 Pq.close()

@@ -92,6 +92,35 @@ template <int BYTES> __device__ __forceinline__ void cp_async(void *smem, const 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// Programmatic dependent launch (sm_90 and later).  The passes of an apply are
+// launched with programmatic stream serialization: each pass kernel triggers its
+// dependents as its blocks start, so once the last wave of a pass is resident
+// the next pass's blocks may be scheduled into the slots that free up; they wait
+// (griddepcontrol.wait) for the previous grid to complete and its memory to be
+// visible before their first global access.  Launched without the attribute,
+// both instructions are no-ops.
+__device__ __forceinline__ void pdl_wait_and_trigger()
+{
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args)
+{
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // xfwd: w_f of one grid row per line, FFT along x (pruned), 4 fields in turn.
 template <typename R, int L>
 __global__ void __launch_bounds__(256) k2_xfwd(const typename cplx_of<R>::type *__restrict__ x,
@@ -100,6 +129,7 @@ __global__ void __launch_bounds__(256) k2_xfwd(const typename cplx_of<R>::type *
                                                typename cplx_of<R>::type *__restrict__ W1, int nrows,
                                                const typename cplx_of<R>::type *__restrict__ tw)
 {
+    pdl_wait_and_trigger();
     using C = typename cplx_of<R>::type;
     constexpr int E = line_elems(L), H = E / 2;
     constexpr int T = L / E, n = L / 2, LPB = 256 / T > 0 ? 256 / T : 1, LS = L + L / 8;
@@ -166,6 +196,7 @@ __global__ void __launch_bounds__(tx_of<R, L>::v * L / line_elems(L)) k2_cols(co
                                                 int nout, long inner, int F, long ib, long if_, long iz, long ob,
                                                 long of, long oz, const typename cplx_of<R>::type *__restrict__ tw)
 {
+    pdl_wait_and_trigger();
     using C = typename cplx_of<R>::type;
     constexpr int E = line_elems(L), H = E / 2;
     constexpr int T = L / E, TX = tx_of<R, L>::v;
@@ -196,6 +227,7 @@ __global__ void __launch_bounds__(tx_of<R, L>::v * L / 8) k2_cols2(const typenam
                                                                  int nout, long inner, int F, long ib, long if_, long iz, long ob,
                                                                  long of, long oz, const typename cplx_of<R>::type *__restrict__ tw)
 {
+    pdl_wait_and_trigger();
     using C = typename cplx_of<R>::type;
     constexpr int T = L / 8, TX = tx_of<R, L>::v;
     extern __shared__ unsigned char smem_raw[];
@@ -234,6 +266,7 @@ __global__ void __launch_bounds__(tx_of<R, L>::v * L / line_elems(L)) k2_zprod1(
                                                  const typename cplx_of<R>::type *__restrict__ spec,
                                                  const typename cplx_of<R>::type *__restrict__ tw)
 {
+    pdl_wait_and_trigger();
     using C = typename cplx_of<R>::type;
     constexpr int E = line_elems(L), H = E / 2;
     constexpr int T = L / E, TX = tx_of<R, L>::v, n = L / 2, n1 = n + 1;
@@ -301,6 +334,7 @@ __global__ void __launch_bounds__(tx_of<R, L>::v * L / 8) k2_zprod4(typename cpl
                                                                   const typename cplx_of<R>::type *__restrict__ spec,
                                                                   const typename cplx_of<R>::type *__restrict__ tw)
 {
+    pdl_wait_and_trigger();
     using C = typename cplx_of<R>::type;
     constexpr int T = L / 8, TX = tx_of<R, L>::v, n = L / 2, n1 = n + 1;
     constexpr long L2 = (long)L * L, oct = (long)n1 * n1 * n1, fs = (long)n * L * L;
@@ -352,6 +386,7 @@ __global__ void __launch_bounds__(256) k2_xinv(const typename cplx_of<R>::type *
                                                typename cplx_of<R>::type *__restrict__ y, long nrows,
                                                const typename cplx_of<R>::type *__restrict__ tw)
 {
+    pdl_wait_and_trigger();
     using C = typename cplx_of<R>::type;
     constexpr int E = line_elems(L), H = E / 2;
     constexpr int T = L / E, n = L / 2, LPB = 256 / T > 0 ? 256 / T : 1, LS = L + L / 8;
@@ -480,6 +515,7 @@ __global__ void __launch_bounds__(tx_of<R, L>::v * L / line_elems(L)) k2_ztma(co
         mbar_fence_init();
     }
     __syncthreads();
+    pdl_wait_and_trigger();
     if (threadIdx.x == 0) {
         if ((int)blockIdx.x < ntiles) issue(blockIdx.x, 0);
         if ((int)(blockIdx.x + gridDim.x) < ntiles) issue(blockIdx.x + gridDim.x, 1);
@@ -597,7 +633,7 @@ spm_status launch_ztma(typename cplx_of<R>::type *W2, const typename cplx_of<R>:
     }
     const int tiles_per_rhs = L * L / TX, ntiles = tiles_per_rhs * nb;
     const int grid = std::min(ntiles, grid_per_sm * sms);
-    k2_ztma<R, L><<<grid, THR, smem, s>>>(map, W2, spec, tw, ntiles, tiles_per_rhs, err);
+    launch_pdl(k2_ztma<R, L>, dim3(grid), dim3(THR), smem, s, map, W2, spec, tw, ntiles, tiles_per_rhs, err);
     return SPM_OK;
 }
 
@@ -633,14 +669,15 @@ spm_status apply_chunk_v2(const typename cplx_of<R>::type *xb, typename cplx_of<
     const int THR = TX * T; // threads of a strided-pass block
     {
         long rows = (long)nb * n2;
-        k2_xfwd<R, L><<<(unsigned)((rows + LPB - 1) / LPB), LPB * T, sm_rows, s>>>(xb, m, p, W1, (int)rows, tw);
+        launch_pdl(k2_xfwd<R, L>, dim3((unsigned)((rows + LPB - 1) / LPB)), dim3(LPB * T), sm_rows, s, xb, m, p, W1,
+                   (int)rows, tw);
     }
     if constexpr (line_elems(L) == 8 && n % 2 == 0)
-        k2_cols2<R, L, -1, true><<<dim3(L / TX, n / 2, nb * 4), THR, 2 * sm_cols, s>>>(
-            W1, W2, L, L, 4, 4 * n2 * L, n2 * L, n * (long)L, 4 * (long)n * L2, (long)n * L2, L2, tw);
+        launch_pdl(k2_cols2<R, L, -1, true>, dim3(L / TX, n / 2, nb * 4), dim3(THR), 2 * sm_cols, s, (const C *)W1, W2,
+                   L, (long)L, 4, 4 * n2 * L, n2 * L, n * (long)L, 4 * (long)n * L2, (long)n * L2, L2, tw);
     else
-        k2_cols<R, L, -1, true><<<dim3(L / TX, n, nb * 4), THR, sm_cols, s>>>(
-            W1, W2, L, L, 4, 4 * n2 * L, n2 * L, n * (long)L, 4 * (long)n * L2, (long)n * L2, L2, tw);
+        launch_pdl(k2_cols<R, L, -1, true>, dim3(L / TX, n, nb * 4), dim3(THR), sm_cols, s, (const C *)W1, W2, L,
+                   (long)L, 4, 4 * n2 * L, n2 * L, n * (long)L, 4 * (long)n * L2, (long)n * L2, L2, tw);
     bool done = false;
     if constexpr (L >= 32) {
         if (zvar == ZPROD_TMA) {
@@ -650,20 +687,21 @@ spm_status apply_chunk_v2(const typename cplx_of<R>::type *xb, typename cplx_of<
     }
     if constexpr (line_elems(L) == 8) {
         if (!done && zvar == ZPROD_FOUR) {
-            k2_zprod4<R, L><<<dim3((unsigned)(L2 / TX), nb), THR, sm_zprod4, s>>>(W2, spec, tw);
+            launch_pdl(k2_zprod4<R, L>, dim3((unsigned)(L2 / TX), nb), dim3(THR), sm_zprod4, s, W2, spec, tw);
             done = true;
         }
     }
-    if (!done) k2_zprod1<R, L><<<dim3((unsigned)(L2 / TX), nb), THR, sm_zprod, s>>>(W2, spec, tw);
+    if (!done) launch_pdl(k2_zprod1<R, L>, dim3((unsigned)(L2 / TX), nb), dim3(THR), sm_zprod, s, W2, spec, tw);
     if constexpr (line_elems(L) == 8 && n % 2 == 0)
-        k2_cols2<R, L, 1, false><<<dim3(L / TX, n / 2, nb * 3), THR, 2 * sm_cols, s>>>(
-            W2, W1, n, L, 3, 4 * (long)n * L2, (long)n * L2, L2, 3 * n2 * L, n2 * L, n * (long)L, tw);
+        launch_pdl(k2_cols2<R, L, 1, false>, dim3(L / TX, n / 2, nb * 3), dim3(THR), 2 * sm_cols, s, (const C *)W2, W1,
+                   n, (long)L, 3, 4 * (long)n * L2, (long)n * L2, L2, 3 * n2 * L, n2 * L, n * (long)L, tw);
     else
-        k2_cols<R, L, 1, false><<<dim3(L / TX, n, nb * 3), THR, sm_cols, s>>>(
-            W2, W1, n, L, 3, 4 * (long)n * L2, (long)n * L2, L2, 3 * n2 * L, n2 * L, n * (long)L, tw);
+        launch_pdl(k2_cols<R, L, 1, false>, dim3(L / TX, n, nb * 3), dim3(THR), sm_cols, s, (const C *)W2, W1, n,
+                   (long)L, 3, 4 * (long)n * L2, (long)n * L2, L2, 3 * n2 * L, n2 * L, n * (long)L, tw);
     {
         long rows = (long)nb * 3 * n2;
-        k2_xinv<R, L><<<(unsigned)((rows + LPB - 1) / LPB), LPB * T, sm_rows, s>>>(W1, xb, yb, rows, tw);
+        launch_pdl(k2_xinv<R, L>, dim3((unsigned)((rows + LPB - 1) / LPB)), dim3(LPB * T), sm_rows, s, (const C *)W1,
+                   xb, yb, rows, tw);
     }
     return SPM_OK;
 }
@@ -1014,6 +1052,7 @@ __global__ void __launch_bounds__(Q_THREADS) k_q(const typename cplx_of<R>::type
                                                  typename cplx_of<R>::type *__restrict__ y, int n, int face_blocks,
                                                  int edge_blocks, int nedge)
 {
+    pdl_wait_and_trigger();
     using C = typename cplx_of<R>::type;
     __shared__ C sv[Q_SMEM];
     const long n3 = (long)n * n * n;
@@ -1046,8 +1085,8 @@ spm_status apply_Q_typed(spm_problem_s *P, const void *vv, void *yv, int nrhs, c
     const int face_blocks = 6 * ((m + QF_U - 1) / QF_U) * ((m + QF_W - 1) / QF_W);
     const int nedge = 12 * m + 8;
     const int edge_blocks = (nedge + Q_THREADS / 32 - 1) / (Q_THREADS / 32);
-    k_q<R><<<dim3((unsigned)(face_blocks + edge_blocks + interior_blocks), (unsigned)nrhs), Q_THREADS, 0, s>>>(
-        v, qa, qtab, y, n, face_blocks, edge_blocks, nedge);
+    launch_pdl(k_q<R>, dim3((unsigned)(face_blocks + edge_blocks + interior_blocks), (unsigned)nrhs), dim3(Q_THREADS), 0,
+               s, v, qa, qtab, y, n, face_blocks, edge_blocks, nedge);
     SPM_CUDA_TRY(cudaGetLastError());
     return SPM_OK;
 }

@@ -99,9 +99,15 @@ static inline int ilog2(int v)
 }
 
 // ------------------------------------------------------------ device buffer
+// Owned device allocation: freed by release() or when the owner goes out of
+// scope (a local work buffer of a call is returned on every exit path).
 struct DevBuf {
     void *ptr = nullptr;
     size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
     spm_status ensure(size_t want);
     void release();
     template <typename T> T *as() const { return reinterpret_cast<T *>(ptr); }
