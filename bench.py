@@ -397,6 +397,29 @@ def run_uneven(args, torch, spm, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+def time_solve_S(spm, torch, P, prec_factor, nrhs=1, reps=10):
+    """Device time of one S^-1 (forward and backward sweep of the factor) and
+    the bandwidth it reaches reading the stored blocks once."""
+    n = P.n
+    x = torch.randn(nrhs, 3, n, n, n, dtype=torch.complex64, device="cuda")
+    y = torch.zeros_like(x)
+    stream = torch.cuda.current_stream()
+    P.solve_S(x, y)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        P.solve_S(x, y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    nbytes = P.factor_bytes(prec_factor)
+    peak, _ = peaks()
+    gbs = nbytes / (ms / 1000.0) / 1e9
+    return {"ms": ms, "factor_bytes": nbytes, "achieved_gbs": gbs, "frac_of_hbm_peak": gbs / peak}
+
+
 def measure_solve(spm, torch, P, wl, args, have_c64_factor):
     """Time-to-1e-6 of the preconditioned solve (set-up reported separately)."""
     out = {"tol": 1e-6, "restart": 20, "nrhs": int(wl["einc"].shape[0])}
@@ -425,6 +448,7 @@ def measure_solve(spm, torch, P, wl, args, have_c64_factor):
             times.append(time.perf_counter() - t1)
         out[name] = {"time_s": float(np.median(times)), "iterations": info.iterations,
                      "outer_steps": info.outer_steps, "true_relres": info.true_relres, "status": st}
+    out["s_inverse_c64"] = time_solve_S(spm, torch, P, spm.SPM_C64)
     # the same mixed solve with the factor's blocks stored as scaled binary16
     t1 = time.perf_counter()
     P.factor_S(spm.SPM_C64H)
@@ -440,6 +464,7 @@ def measure_solve(spm, torch, P, wl, args, have_c64_factor):
         times.append(time.perf_counter() - t1)
     out["mixed_half_factor"] = {"time_s": float(np.median(times)), "iterations": info.iterations,
                                 "outer_steps": info.outer_steps, "true_relres": info.true_relres, "status": st}
+    out["s_inverse_c64_half"] = time_solve_S(spm, torch, P, spm.SPM_C64)
     if "fp64" in out:
         out["fp64_over_mixed"] = out["fp64"]["time_s"] / out["mixed"]["time_s"]
         out["fp64_over_mixed_half_factor"] = out["fp64"]["time_s"] / out["mixed_half_factor"]["time_s"]

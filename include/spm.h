@@ -186,6 +186,7 @@ typedef struct {
     int half_store;
     int raised_pivots;      /* pivots raised by the static perturbation in the kept factor */
     double probe_relres;
+    long long stored_bytes; /* bytes of the stored blocks; each S^{-1} reads them once */
 } spm_factor_report;
 spm_status spm_factor_info(spm_problem prob, spm_prec prec, spm_factor_report *out);
 

@@ -65,7 +65,8 @@ class SpmError(RuntimeError):
 
 class FactorReport(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int), ("attempts", ctypes.c_int), ("half_store", ctypes.c_int),
-                ("raised_pivots", ctypes.c_int), ("probe_relres", ctypes.c_double)]
+                ("raised_pivots", ctypes.c_int), ("probe_relres", ctypes.c_double),
+                ("stored_bytes", ctypes.c_longlong)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -261,6 +262,12 @@ class Problem:
         r = FactorReport()
         _check(lib.spm_factor_info(self.h, prec, ctypes.byref(r)))
         return r.variant, r.attempts, bool(r.half_store), r.probe_relres, r.raised_pivots
+
+    def factor_bytes(self, prec=SPM_C64):
+        """Bytes of the stored factor blocks in ``prec`` (read once by each S^-1)."""
+        r = FactorReport()
+        _check(lib.spm_factor_info(self.h, prec, ctypes.byref(r)))
+        return r.stored_bytes
 
     def apply_S(self, x, y, stream=None):
         _check(lib.spm_apply_S(self.h, _prec_of(x), _ptr(x), _ptr(y), _nrhs(x, self.n), _stream(stream)))

@@ -380,6 +380,7 @@ extern "C" spm_status spm_factor_info(spm_problem P, spm_prec prec, spm_factor_r
     out->half_store = P->fac_info[fi].half_store ? 1 : 0;
     out->probe_relres = P->fac_info[fi].probe_relres;
     out->raised_pivots = P->fac_info[fi].raised_pivots;
+    out->stored_bytes = (long long)P->fac_info[fi].stored_bytes;
     return SPM_OK;
 }
 

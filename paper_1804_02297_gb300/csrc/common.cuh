@@ -145,7 +145,12 @@ struct spm_problem_s {
     bool have_S = false;
     DevBuf S128, S64; // [n^3][27][3][3] complex; absent neighbours hold zeros
     NDFactor *fac128 = nullptr, *fac64 = nullptr;
-    struct FactorInfo { int variant = -1, attempts = 0, raised_pivots = 0; double probe_relres = 0; bool half_store = false; };
+    struct FactorInfo {
+        int variant = -1, attempts = 0, raised_pivots = 0;
+        double probe_relres = 0;
+        bool half_store = false;
+        size_t stored_bytes = 0;
+    };
     FactorInfo fac_info[2]; // [0] complex128 factor, [1] complex64 factor
 
     // solver workspace

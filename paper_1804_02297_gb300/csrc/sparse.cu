@@ -375,6 +375,7 @@ struct NDFactor {
     int prec = 0;
     int variant = 0;         // nested-dissection tree variant (cut offsets)
     int raised_pivots = 0;   // pivots raised by the static perturbation
+    size_t stored_bytes = 0; // bytes of the stored blocks (G and X, plus half-storage scales)
     bool half_store = false; // blocks as scaled binary16 pairs (complex64 factor only)
     DevBuf scales;           // per-column scales (half storage)
     int n = 0;
@@ -569,6 +570,8 @@ static spm_status factor_typed(spm_problem_s *P, NDFactor *F, bool half_store, i
     if (!rels.empty())
         SPM_CUDA_TRY(cudaMemcpy(F->rels.ptr, rels.data(), sizeof(int) * rels.size(), cudaMemcpyHostToDevice));
     SPM_TRY(F->fac.ensure((half_store ? sizeof(__half2) : sizeof(C)) * fac_total));
+    F->stored_bytes = (half_store ? sizeof(__half2) : sizeof(C)) * (size_t)fac_total +
+                      (half_store ? sizeof(float) * (size_t)scale_total : 0);
     DevBuf gx; // complex64 staging of G and X before conversion (half storage)
     if (half_store) {
         SPM_TRY(gx.ensure(sizeof(C) * max_gx));
@@ -933,6 +936,7 @@ spm_status spm_factor_impl(spm_problem_s *P, int prec)
     P->fac_info[fi].variant = best_v;
     P->fac_info[fi].attempts = attempts;
     P->fac_info[fi].raised_pivots = slot->raised_pivots;
+    P->fac_info[fi].stored_bytes = slot->stored_bytes;
     P->fac_info[fi].probe_relres = best;
     P->fac_info[fi].half_store = prec == SPM_C64H;
     return SPM_OK;
@@ -953,6 +957,7 @@ spm_status spm_factor_tree_impl(spm_problem_s *P, int prec, int variant)
     P->fac_info[fi].variant = variant;
     P->fac_info[fi].attempts = 1;
     P->fac_info[fi].raised_pivots = slot->raised_pivots;
+    P->fac_info[fi].stored_bytes = slot->stored_bytes;
     P->fac_info[fi].probe_relres = r;
     P->fac_info[fi].half_store = prec == SPM_C64H;
     return SPM_OK;
