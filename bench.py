@@ -167,7 +167,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(wl, seconds, op, max_steps=None, warmup=1):
+def cpu_baseline(wl, seconds, op, max_steps=None, warmup=1, single_thread_seconds=0.0):
     """FP64 oracle apply (A, then Q for op QA) on a bounded sample: `warmup`
     untimed applies, then whole timed applies until about `seconds` have passed
     (or `max_steps` applies).  For Q the stencil tables are seeded random
@@ -195,12 +195,26 @@ def cpu_baseline(wl, seconds, op, max_steps=None, warmup=1):
         if time.perf_counter() - t0 > seconds:
             break
     dt = time.perf_counter() - t0
-    F.close()
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     what = "A then Q" if op == "QA" else "A"
-    return {"value": count / dt, "unit": "applies/s", "cores": cores, "kind": "oracle", "steps_run": count,
-            "sample": f"{count} FP64 oracle applies of {what} at n={n} (kernel spectra precomputed), "
-                      f"{dt:.1f} s on {cores} host threads"}
+    out = {"value": count / dt, "unit": "applies/s", "cores": cores, "kind": "oracle", "steps_run": count,
+           "sample": f"{count} FP64 oracle applies of {what} at n={n} (kernel spectra precomputed), "
+                     f"{dt:.1f} s on {cores} host threads"}
+    if single_thread_seconds > 0:
+        oracle.set_threads(1)
+        t0 = time.perf_counter()
+        c1 = 0
+        while True:
+            one()
+            c1 += 1
+            if time.perf_counter() - t0 > single_thread_seconds:
+                break
+        d1 = time.perf_counter() - t0
+        oracle.set_threads(cores)
+        out["single_thread"] = {"value": c1 / d1, "unit": "applies/s", "cores": 1,
+                                "sample": f"{c1} applies, {d1:.1f} s on one host thread"}
+    F.close()
+    return out
 
 
 def run_reference(args):
@@ -604,7 +618,7 @@ def run_ours(args):
         line["solve"] = measure_solve(spm, torch, P, wl, args, True)
         line["solve"]["setup"] = setup
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds, args.op)
+        line["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds, args.op, single_thread_seconds=5.0)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -40,6 +40,8 @@ def lib():
         D = ctypes.c_double
         L.spmref_lattice_zeta.restype = D
         L.spmref_lattice_zeta.argtypes = [D]
+        L.spmref_set_threads.argtypes = [I]
+        L.spmref_set_threads.restype = None
         L.spmref_kernel_entries.argtypes = [I, D, I, P]
         L.spmref_medium.argtypes = [I, P, P, P, P]
         L.spmref_apply_direct.argtypes = [I, D, I, P, P, P, P]
@@ -256,3 +258,8 @@ def gmres(n, k, m, p, b, tol=1e-12, maxit=500, restart=500, quad=QUAD_ORDER4,
                             int(maxit), int(restart), sfactor.h if sfactor else None,
                             _p(al) if al is not None else None, ctypes.byref(rel), _p(hist))
     return x, it, rel.value, hist[:it]
+
+
+def set_threads(t):
+    """OpenMP thread count of the oracle's loops (used only to time it)."""
+    lib().spmref_set_threads(int(t))

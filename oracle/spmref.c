@@ -30,6 +30,9 @@
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef double complex cplx;
 #define PI 3.14159265358979323846264338327950288
@@ -984,4 +987,15 @@ int spmref_gmres(int n, double k, int quad, const cplx *m, const cplx *p,
     free(V); free(H); free(cs); free(sn); free(gvec); free(r); free(t);
     (void)k; (void)quad;
     return it;
+}
+
+/* Thread count of the OpenMP loops above, for timing the oracle: every
+   parallel loop writes disjoint outputs, so results do not depend on it. */
+void spmref_set_threads(int t)
+{
+#ifdef _OPENMP
+    if (t > 0) omp_set_num_threads(t);
+#else
+    (void)t;
+#endif
 }

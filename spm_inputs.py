@@ -236,11 +236,11 @@ def workload(name: str):
         k = wavenumber_for_grid(n)
         eps, grad = medium_bumps(n, seed=5, count=32)
         einc = plane_wave_block(n, k, 8)
-    elif name == "n256_bumps32":
+    elif name in ("n256_bumps32", "n256_bumps32_rhs8"):
         n = 256
         k = wavenumber_for_grid(n)
         eps, grad = medium_bumps(n, seed=6, count=32)
-        einc = plane_wave(n, k, (0, 0, 1), (1, 0, 0))[None]
+        einc = plane_wave(n, k, (0, 0, 1), (1, 0, 0))[None] if name == "n256_bumps32" else plane_wave_block(n, k, 8)
     else:
         raise KeyError(name)
     return dict(n=n, omega=k, eps=eps, grad=grad, einc=einc)
