@@ -251,7 +251,9 @@ spm_status spm_rhs_from_incident(spm_problem prob, const void *einc_dev, void *g
  * g_dev, x_dev: complex128, nrhs x 3 x n^3; x_dev is the initial guess on entry.
  * restart <= 0 selects 20 (Section 4).  Returns SPM_ERR_NO_CONVERGENCE with the
  * last iterate in x_dev if maxit inner iterations per RHS are exceeded.
- * Synchronises. */
+ * The GMRES vectors ((restart + 3) x nrhs fields in the inner precision, plus
+ * two FP64 fields per RHS) live in a problem-owned buffer that grows to the
+ * largest solve and is freed by spm_destroy.  Synchronises. */
 spm_status spm_solve(spm_problem prob, spm_prec prec, const void *g_dev, void *x_dev, int nrhs,
                      double tol, int maxit, int restart, spm_solve_info *info);
 

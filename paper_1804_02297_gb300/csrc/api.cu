@@ -209,7 +209,7 @@ extern "C" spm_status spm_destroy(spm_problem P)
     P->spec128.release(); P->spec64.release(); P->tw128.release(); P->tw64.release();
     P->work.release(); P->alpha128.release(); P->alpha64.release(); P->beta128.release();
     P->qtab128.release(); P->qtab64.release();
-    P->S128.release(); P->S64.release(); P->kry.release(); P->dev_err.release();
+    P->S128.release(); P->S64.release(); P->kry.release(); P->gmres_ws.release(); P->dev_err.release();
     spm_factor_free(P->fac128);
     spm_factor_free(P->fac64);
     delete P;

@@ -3,7 +3,8 @@
 // row combination Q (Eq. nbr_i_block_alpha).
 //
 // Five passes per chunk of right-hand sides, each a batch of 1-D FFTs along
-// one axis done in shared memory (fft.cuh):
+// one axis, register-resident with shared-memory exchanges between stages
+// (fft_reg.cuh; fft.cuh serves only the one-time FP64 kernel spectra):
 //   xfwd : w = [m E^1, m E^2, m E^3, p.E] formed on the fly, FFT along x
 //          (n inputs zero-padded to L = 2n)          -> W1[b][4][z<n][y<n][xi<L]
 //   yfwd : FFT along y (n -> L)                      -> W2[b][4][z<n][eta<L][xi<L]
@@ -27,10 +28,6 @@
 namespace {
 
 constexpr int NT = 256; // threads per block for every FFT pass
-
-template <typename R> struct tile_cfg;
-template <> struct tile_cfg<float> { static constexpr int TXMAX = 16; };
-template <> struct tile_cfg<double> { static constexpr int TXMAX = 8; };
 
 // -------------------------------------------------------------- strided lines
 // Lines along a strided axis.  Element (b, f, z, pos, i) of the input sits at
@@ -105,6 +102,8 @@ __device__ __forceinline__ void pdl_wait_and_trigger()
     asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
 }
 
+// A failed launch sets the runtime's last error, which every apply checks after
+// its launches (cudaGetLastError), as for <<<>>> launches.
 template <typename... KArgs, typename... Args>
 void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args)
 {

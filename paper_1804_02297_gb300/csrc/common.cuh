@@ -154,7 +154,8 @@ struct spm_problem_s {
     FactorInfo fac_info[2]; // [0] complex128 factor, [1] complex64 factor
 
     // solver workspace
-    DevBuf kry;
+    DevBuf kry;      // A x inside apply_QA
+    DevBuf gmres_ws; // GMRES vectors and reductions of spm_solve
 };
 
 // ------------------------------------------------------------ internal API

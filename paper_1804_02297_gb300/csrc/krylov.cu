@@ -359,7 +359,7 @@ spm_status solve_typed(spm_problem_s *P, int mode, const double2 *g, double2 *x,
     size_t bytes = sizeof(double2) * 2 * vstride + sizeof(C) * (size_t)(restart + 3) * vstride +
                    sizeof(double2) * (size_t)nrhs * DOT_BLOCKS * VGROUP + sizeof(double2) * nrhs * ld +
                    sizeof(double) * nrhs + 256 * 8;
-    DevBuf ws;
+    DevBuf &ws = P->gmres_ws; // kept across solves: sized by the largest solve so far
     SPM_TRY(ws.ensure(bytes));
     char *p = ws.as<char>();
     double2 *r = reinterpret_cast<double2 *>(p); p += sizeof(double2) * vstride;
