@@ -54,3 +54,31 @@ def test_argument_validation_without_gpu(spm):
     assert lib.spm_apply_A(None, 0, None, None, 1, None) == spm.SPM_ERR_INVALID_ARG
     assert lib.spm_solve(None, 0, None, None, 1, 1e-6, 10, 20, None) == spm.SPM_ERR_INVALID_ARG
     assert lib.spm_destroy(None) == spm.SPM_OK
+
+
+def test_host_side_settings_without_gpu(spm):
+    """Process-wide settings that touch no device: the apply plan table and the
+    factor GEMM mode round-trip, and invalid values are refused."""
+    lib = spm.lib
+    saved = spm.get_apply_plan(spm.SPM_C64, 128)
+    try:
+        for z in (spm.ZPASS_FOUR, spm.ZPASS_ONE, spm.ZPASS_TMA, -1):
+            spm.set_apply_plan(spm.SPM_C64, 128, z)
+            assert spm.get_apply_plan(spm.SPM_C64, 128) == z
+    finally:
+        spm.set_apply_plan(spm.SPM_C64, 128, saved)
+    assert lib.spm_set_apply_plan(spm.SPM_C64, 96, spm.ZPASS_FOUR) == spm.SPM_ERR_INVALID_ARG  # radix-3 length
+    assert lib.spm_set_apply_plan(spm.SPM_C64, 16, spm.ZPASS_TMA) == spm.SPM_ERR_INVALID_ARG  # too short for TMA
+    assert lib.spm_set_apply_plan(spm.SPM_C64, 100, spm.ZPASS_ONE) == spm.SPM_ERR_INVALID_ARG  # no such length
+    assert lib.spm_set_apply_plan(spm.SPM_MIXED, 128, spm.ZPASS_ONE) == spm.SPM_ERR_INVALID_ARG
+    mode = spm.get_factor_gemm()
+    try:
+        spm.set_factor_gemm(1)
+        assert spm.get_factor_gemm() == 1
+    finally:
+        spm.set_factor_gemm(mode)
+    assert lib.spm_set_factor_gemm(2) == spm.SPM_ERR_INVALID_ARG
+    rep = spm.FactorReport()
+    assert lib.spm_factor_info(None, spm.SPM_C64, ctypes.byref(rep)) == spm.SPM_ERR_INVALID_ARG
+    assert lib.spm_device_status(None) == spm.SPM_ERR_INVALID_ARG
+    assert lib.spm_selftest_bounded_wait(None) == spm.SPM_ERR_INVALID_ARG
