@@ -40,6 +40,7 @@ def lib():
         D = ctypes.c_double
         L.spmref_lattice_zeta.restype = D
         L.spmref_lattice_zeta.argtypes = [D]
+        L.spmref_apply_direct_points.argtypes = [I, D, I, P, P, P, I, P, P]
         L.spmref_set_threads.argtypes = [I]
         L.spmref_set_threads.restype = None
         L.spmref_kernel_entries.argtypes = [I, D, I, P]
@@ -111,6 +112,16 @@ def apply_direct(n, k, m, p, x, quad=QUAD_ORDER4):
     y = np.zeros_like(x)
     lib().spmref_apply_direct(n, float(k), quad, _p(m), _p(p), _p(x), _p(y))
     return y
+
+
+def apply_direct_points(n, k, m, p, x, idx, quad=QUAD_ORDER4):
+    """(A x)[:, i] for the linear point indices idx by the direct sum (entries
+    evaluated on the fly); returns an array of shape (len(idx), 3)."""
+    x = _c(x); m = _c(m); p = _c(p)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    out = np.zeros((len(idx), 3), np.complex128)
+    lib().spmref_apply_direct_points(n, float(k), quad, _p(m), _p(p), _p(x), len(idx), _p(idx), _p(out))
+    return out
 
 
 def apply_fft(n, k, m, p, x, quad=QUAD_ORDER4):

@@ -245,6 +245,32 @@ void spmref_apply_direct(int n, double k, int quad, const cplx *m, const cplx *p
     free(e.tab);
 }
 
+/* (A x) at selected points only: the same direct sum of Eq. (discrete) as
+   spmref_apply_direct, term for term and in the same order, with each kernel
+   entry evaluated when it is needed instead of from the full (2n-1)^3 table
+   (for large n, where the table and the full O(N^2) sum are out of reach).
+   idx: npts linear point indices (i1 fastest); out: npts x 3. */
+void spmref_apply_direct_points(int n, double k, int quad, const cplx *m, const cplx *p, const cplx *x,
+                                int npts, const long *idx, cplx *out)
+{
+    long N = (long)n * n * n;
+    double h = 1.0 / (n + 1), k2 = k * k;
+#pragma omp parallel for schedule(dynamic)
+    for (int s = 0; s < npts; ++s) {
+        long i = idx[s];
+        int i1 = i % n, i2 = (i / n) % n, i3 = i / ((long)n * n);
+        cplx acc[3] = {0, 0, 0};
+        for (long j = 0; j < N; ++j) {
+            int j1 = j % n, j2 = (j / n) % n, j3 = j / ((long)n * n);
+            cplx v[4];
+            kernel_entry(i1 - j1, i2 - j2, i3 - j3, h, k, quad, v);
+            cplx w4 = p[j] * x[j] + p[N + j] * x[N + j] + p[2 * N + j] * x[2 * N + j];
+            for (int d = 0; d < 3; ++d) acc[d] += k2 * v[0] * (m[j] * x[d * N + j]) + v[1 + d] * w4;
+        }
+        for (int d = 0; d < 3; ++d) out[3 * s + d] = x[d * N + i] + acc[d];
+    }
+}
+
 /* ===================================================================== */
 /* Radix-2 FFT (iterative Cooley-Tukey) and 3-D transforms.               */
 /* ===================================================================== */

@@ -113,6 +113,20 @@ def test_identity_in_vacuum():
     assert np.array_equal(oracle.apply_direct(n, 3.0, m, p, x), x)
 
 
+@pytest.mark.parametrize("quad", [0, 1])
+def test_sampled_direct_sum_equals_full_direct_sum(quad):
+    """The sampled direct sum (entries evaluated on the fly, used at full grid
+    sizes) gives exactly the full direct sum's outputs at every point, corners,
+    edges, faces and interior alike."""
+    n, k = 6, 2.2
+    m, p = _medium(n, seed=21)
+    x = si.random_field(n, 22)
+    full = oracle.apply_direct(n, k, m, p, x, quad=quad).reshape(3, -1)
+    idx = np.arange(n ** 3)
+    pts = oracle.apply_direct_points(n, k, m, p, x, idx, quad=quad)
+    assert np.max(np.abs(pts.T - full)) <= 1e-14 * np.max(np.abs(full))
+
+
 @pytest.mark.parametrize("n", [4, 5, 7, 8])
 def test_direct_sum_equals_fft_apply(n):
     """O(N^2) summation of Eq. (discrete) equals the circulant-embedded FFT apply."""
