@@ -10,9 +10,18 @@ combination Q; ``--op A`` applies A alone.
 
 ``solve`` (same JSON line): time to a true relative residual of 1e-6 for the
 workload's incident field with the S^-1 Q preconditioned GMRES(20), complex64
-operator and factor inside the FP64 outer loop (``mixed``); ``--solve both``
-adds the plain complex128 solve.  Set-up (stencils, factor) is timed apart from
-the solve, as the paper reports T_setup apart from T_solve.
+operator and factor inside the FP64 outer loop (``mixed``) and plain complex128
+throughout (``fp64``, the default ``--solve both``; ``--solve mixed`` skips the
+complex128 factor), with their ratio ``fp64_over_mixed``.  Set-up (stencils,
+factor) is timed apart from the solve, as the paper reports T_setup apart from
+T_solve.  ``solve_block64`` does the same for the 64 plane waves of the n = 64
+medium as one block right-hand side (mixed vs FP64 batched time-to-solution).
+``apply_n256`` times the n = 256 apply of A (L = 512), where the pass
+intermediates stream through HBM, against the measured HBM and FP32 peaks.
+
+Roofline denominators: HBM from MEASURED_PEAKS.json (copy bandwidth); FP32 and
+FP64 measured in the same process by the library's FMA micro-benchmark
+(``spm_measure_peak``).
 
 Timing: W warm-up steps, then K steps, each bracketed by CUDA events on the
 launch stream, with an L2 flush (a 512 MiB buffer write) between steps, barrier
@@ -53,7 +62,11 @@ def parse():
     ap.add_argument("--workload", default="n64_bumps8")
     ap.add_argument("--prec", default="c64", choices=["c64", "c128"])
     ap.add_argument("--op", default="QA", choices=["A", "QA"])
-    ap.add_argument("--solve", default="mixed", choices=["none", "mixed", "both"])
+    ap.add_argument("--solve", default="both", choices=["none", "mixed", "both"])
+    ap.add_argument("--no-block-solve", action="store_true",
+                    help="skip the 64-RHS block solve (config 3) in the default n = 64 run")
+    ap.add_argument("--no-n256", action="store_true",
+                    help="skip the n = 256 apply sub-measurement of the default run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--uneven-solve-all", action="store_true",
@@ -76,8 +89,21 @@ def compulsory_bytes(n, prec, nrhs=1):
     return el * (nrhs * 3 * N + N + 3 * N + 4 * (n + 1) ** 3 + nrhs * 3 * N)
 
 
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
-FP64_PEAK_TFLOPS = 1.25  # GB300 FP64 rate (tensor and CUDA cores), nominal
+def alu_peaks(spm, torch):
+    """FP32 and FP64 peaks of this GPU, measured in this process by the library's
+    FMA micro-benchmark (spm_measure_peak: independent register FMA chains on
+    every SM, best of five launches of a few ms).  The FP32 peak is the larger of
+    the scalar FFMA and the packed FP32x2 FFMA rates.  The SM count comes from
+    the device; the derived figure (SMs x 128 FP32 lanes x 2 x max SM clock) is
+    reported beside the measurement."""
+    f1, m1 = spm.measure_peak(spm.PEAK_FFMA)
+    f2, m2 = spm.measure_peak(spm.PEAK_FFMA2)
+    d1, m3 = spm.measure_peak(spm.PEAK_DFMA)
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    sms = props.multi_processor_count
+    return {"fp32": max(f1, f2), "fp64": d1, "fp32_ffma": f1, "fp32_ffma2": f2, "fp64_dfma": d1,
+            "sms": sms, "fp32_derived_at_2070MHz": sms * 128 * 2 * 2.070e9 / 1e12,
+            "source": "measured: spm_measure_peak FMA micro-benchmark, this run"}
 
 
 def algorithmic_flops(n, op, nrhs=1):
@@ -324,7 +350,8 @@ def run_uneven(args, torch, spm, rank, world, local):
     peak, peak_kind = peaks()
     achieved = alg / (ms_per_step / 1000.0) / 1e9
     flops = sum(algorithmic_flops(q["n"], "A") for q in probs)
-    fpeak = FP32_PEAK_TFLOPS if args.prec == "c64" else FP64_PEAK_TFLOPS
+    apk = alu_peaks(spm, torch)
+    fpeak = apk["fp32"] if args.prec == "c64" else apk["fp64"]
     tflops = flops / (ms_per_step / 1000.0) / 1e12
     line = {"metric": METRIC, "value": value, "unit": "problem applies/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -335,6 +362,7 @@ def run_uneven(args, torch, spm, rank, world, local):
                        "parallelism": f"replicas{world}"},
             "roofline": {"bound": "alu", "kernel": "batched apply_A (graph)", "achieved": tflops, "peak": fpeak,
                          "unit": "TFLOP/s", "frac": tflops / fpeak, "algorithmic_flops": flops, "traffic": None,
+                         "peak_source": apk["source"], "peaks": apk,
                          "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                                  "peak_source": peak_kind, "algorithmic_bytes": alg}},
             "gpu_launches": 5 * len(probs) * args.steps, "clocks": clocks}
@@ -485,6 +513,87 @@ def measure_solve(spm, torch, P, wl, args, have_c64_factor):
     return out
 
 
+def measure_n256(spm, torch, apk, hbm_peak, hbm_kind, steps=12, warmup=3):
+    """The n = 256 apply of A (L = 512, 32 bumps, k = 64 pi, one right-hand side,
+    complex64), where the pass intermediates (24 n^3 complex = 3.2 GB) stream
+    through HBM: device time per apply (CUDA events, L2 flushed between applies),
+    its algorithmic bytes and flops against the measured peaks, and the DRAM
+    bytes ncu recorded for one apply (profiles/apply_dram_traffic.md, while the
+    apply sources are unchanged)."""
+    wl = si.workload("n256_bumps32")
+    n = wl["n"]
+    P = spm.Problem(n, wl["omega"], wl["eps"], wl["grad"])
+    x = torch.from_numpy(wl["einc"]).to(torch.complex64).to("cuda").contiguous()
+    y = torch.zeros_like(x)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(warmup):
+        P.apply_A(x, y)
+    torch.cuda.synchronize()
+    ev = []
+    for _ in range(steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        P.apply_A(x, y)
+        e1.record(stream)
+        ev.append((e0, e1))
+    torch.cuda.synchronize()
+    ms = float(np.median([a.elapsed_time(b) for a, b in ev]))
+    alg = compulsory_bytes(n, "c64")
+    flops = algorithmic_flops(n, "A")
+    traffic = recorded_traffic("n256_bumps32", "c64", "A")
+    out = {"workload": "n256_bumps32", "op": "A", "dtype": "c64", "steps": steps, "ms_per_apply": ms,
+           "applies_per_s": 1000.0 / ms, "zpass": zpass_name(spm, "c64", 2 * n),
+           "algorithmic_bytes": alg, "hbm_frac_algorithmic": alg / (ms / 1000.0) / 1e9 / hbm_peak,
+           "hbm_peak_gbs": hbm_peak, "hbm_peak_source": hbm_kind,
+           "algorithmic_flops": flops, "tflops": flops / (ms / 1000.0) / 1e12,
+           "fp32_frac": flops / (ms / 1000.0) / 1e12 / apk["fp32"], "fp32_peak_tflops": apk["fp32"],
+           "traffic": traffic}
+    if traffic is not None:
+        out["dram_gbs"] = traffic / (ms / 1000.0) / 1e9
+        out["dram_frac"] = out["dram_gbs"] / hbm_peak
+    P.close()
+    del P, x, y, flush
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return out
+
+
+def measure_block_solve(spm, torch, P, args):
+    """Config 3: the 64 incident plane waves (32 Fibonacci directions x 2
+    polarisations) of the n = 64 medium as one block right-hand side, solved to a
+    true relative residual of 1e-6, complex64 operator and factor inside the FP64
+    outer loop (mixed) and plain complex128 (fp64, when --solve both built its
+    factor).  Set-up is shared with the single-RHS solve and not counted."""
+    wl = si.workload("n64_bumps8_rhs64")
+    e = torch.from_numpy(wl["einc"]).to("cuda")
+    g = torch.zeros_like(e)
+    P.rhs_from_incident(e, g)
+    del e
+    out = {"nrhs": int(g.shape[0]), "tol": 1e-6, "restart": 20}
+    modes = [("mixed", spm.SPM_MIXED)] + ([("fp64", spm.SPM_C128)] if args.solve == "both" else [])
+    # the mixed solve with the complex64 factor (the half-storage one was built last)
+    P.factor_S(spm.SPM_C64)
+    for name, prec in modes:
+        x = torch.zeros_like(g)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        info, st = P.solve(g, x, prec=prec, tol=1e-6, maxit=400, restart=20, check=False)
+        torch.cuda.synchronize()
+        out[name] = {"time_s": time.perf_counter() - t1, "iterations": info.iterations,
+                     "outer_steps": info.outer_steps, "true_relres": info.true_relres, "status": st,
+                     "field_solves_per_s": g.shape[0] / (time.perf_counter() - t1)}
+        del x
+    if "fp64" in out:
+        out["fp64_over_mixed"] = out["fp64"]["time_s"] / out["mixed"]["time_s"]
+    del g
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -580,7 +689,8 @@ def run_ours(args):
     achieved = alg / (ms_per_step / 1000.0) / 1e9
     flops = algorithmic_flops(n, args.op, nrhs)
     tflops = flops / (ms_per_step / 1000.0) / 1e12
-    fpeak = FP32_PEAK_TFLOPS if args.prec == "c64" else FP64_PEAK_TFLOPS
+    apk = alu_peaks(spm, torch)
+    fpeak = apk["fp32"] if args.prec == "c64" else apk["fp64"]
     # roofline: the bound whose minimum time is longer (flops at the ALU peak vs
     # compulsory bytes at the measured HBM bandwidth) is the one reported
     alu_bound = flops / (fpeak * 1e12) > alg / (peak * 1e9)
@@ -592,8 +702,8 @@ def run_ours(args):
         hbm["dram_achieved"] = traffic / (ms_per_step / 1000.0) / 1e9
         hbm["dram_frac"] = hbm["dram_achieved"] / peak
     alu = {"achieved": tflops, "peak": fpeak, "unit": "TFLOP/s", "frac": tflops / fpeak,
-           "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if args.prec == "c64"
-           else "nominal GB300 FP64", "algorithmic_flops": flops}
+           "peak_source": apk["source"] + (" (FP32)" if args.prec == "c64" else " (FP64)"),
+           "algorithmic_flops": flops, "peaks": apk}
     roof = dict(alu if alu_bound else hbm)
     roof["bound"] = "alu" if alu_bound else "hbm"
     roof["kernel"] = f"apply_{args.op} ({launches_per_step} launches)"
@@ -617,6 +727,14 @@ def run_ours(args):
     if args.solve != "none" and n <= 64:
         line["solve"] = measure_solve(spm, torch, P, wl, args, True)
         line["solve"]["setup"] = setup
+        if args.workload == "n64_bumps8" and not args.no_block_solve:
+            line["solve_block64"] = measure_block_solve(spm, torch, P, args)
+    if args.workload == "n64_bumps8" and not args.no_n256:
+        fn = None
+        P.close()  # release the n = 64 factors before the n = 256 problem
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        line["apply_n256"] = measure_n256(spm, torch, apk, peak, peak_kind)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds, args.op, single_thread_seconds=5.0)
     if rank == 0:

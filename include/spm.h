@@ -72,7 +72,8 @@ typedef enum { SPM_C128 = 0, SPM_C64 = 1, SPM_MIXED = 2, SPM_C64H = 3 } spm_prec
  * The library forms m = 1 - eps and p^d = (d_d m)/(1 - m) = -d_d eps/eps
  * (Section 2, definitions before Eq. discrete), the four Toeplitz kernels
  * G, G^1, G^2, G^3 and their spectra on a 2n-periodic grid (circulant embedding;
- * FP64, stored in complex128 and complex64).  n must be in [4, 512].
+ * FP64, stored in complex128 and complex64).  n must be in [4, 256] and a
+ * power of two, or 48 or 96 (FFT lengths 2n: powers of two up to 512, 96, 192).
  * Synchronises `stream`.  On success *out is a new handle. */
 spm_status spm_create_problem(int n, double omega, const double *eps_host,
                               const double *grad_eps_host, spm_quad quad,
@@ -101,13 +102,16 @@ spm_status spm_apply_A(spm_problem prob, spm_prec prec, const void *x_dev, void 
  * device).  The pass intermediates live in one fixed 64 MiB device array inside
  * the library (every GPU that loads the library holds it until the process
  * exits); right-hand sides are processed one at a time, so the limit is
- * 24 n^3 complex values: n <= 64 in SPM_C64, n <= 32 in SPM_C128.  Larger
- * problems return SPM_ERR_INVALID_ARG before any device work.  The first call
- * on a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.  All
- * calls share the array: calls whose work overlaps on the GPU (different
- * streams, or different handles at once) race on it and give wrong results.
- * The problem handle itself is created (and allocated) by spm_create_problem. */
+ * 24 n^3 complex values per call: n <= 64 in SPM_C64 and n <= 48 in SPM_C128
+ * (n = 64 in SPM_C128 needs 96 MiB).  Larger problems return
+ * SPM_ERR_INVALID_ARG before any device work.  Every call looks up the array's
+ * device address on the current device (cudaGetSymbolAddress, which allocates
+ * nothing), so the call stays valid across a device reset; make the first call
+ * on a device before any stream capture, since that lookup may initialise the
+ * library's module on the device.  All calls share the array: calls whose work
+ * overlaps on the GPU (different streams, or different handles at once) race on
+ * it and give wrong results.  The problem handle itself is created (and
+ * allocated) by spm_create_problem. */
 spm_status spm_apply_A_noalloc(spm_problem prob, spm_prec prec, const void *x_dev, void *y_dev,
                                int nrhs, void *stream);
 
@@ -295,6 +299,19 @@ spm_status spm_kernel_entries(spm_problem prob, double *out_host);
 
 /* The lattice constant Z used by SPM_QUAD_ORDER4 (computed by Ewald summation). */
 double spm_lattice_constant(void);
+
+/* -------------------------------------------------------- measurement */
+
+/* Measured arithmetic peak of the current device in TFLOP/s (the paper has no
+ * counterpart: this gives the denominators of the ALU roofline the applies are
+ * reported against).  kind 0: FP32 fused multiply-add (FFMA), kind 1: packed
+ * FP32x2 multiply-add (two per instruction), kind 2: FP64 fused multiply-add.
+ * Each runs independent register FMA chains on every SM (2048 threads per SM)
+ * for a few milliseconds and reports the best of five timed launches; *ms_out
+ * (may be NULL) receives that launch's time.  Allocates a small output buffer
+ * and a private stream, synchronises the device's work on that stream only.
+ * SPM_ERR_INVALID_ARG for another kind or a NULL tflops. */
+spm_status spm_measure_peak(int kind, double *tflops, double *ms_out);
 
 /* Thread-local message of the last failing call ("" if none). */
 const char *spm_last_error(void);

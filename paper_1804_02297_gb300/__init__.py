@@ -27,7 +27,7 @@ EXPORTS = [
     "spm_solve_S", "spm_incident_plane_wave", "spm_rhs_from_incident", "spm_solve", "spm_kernel_entries",
     "spm_lattice_constant", "spm_last_error", "spm_apply_A_noalloc",
     "spm_create_batch", "spm_destroy_batch", "spm_batch_size", "spm_batch_problem", "spm_batch_build_stencils",
-    "spm_batch_apply_A", "spm_batch_solve",
+    "spm_batch_apply_A", "spm_batch_solve", "spm_measure_peak",
 ]
 
 
@@ -50,6 +50,16 @@ def get_factor_gemm():
     m = ctypes.c_int()
     _check(lib.spm_get_factor_gemm(ctypes.byref(m)))
     return m.value
+
+
+PEAK_FFMA, PEAK_FFMA2, PEAK_DFMA = 0, 1, 2
+
+
+def measure_peak(kind):
+    """(TFLOP/s, ms of the best launch) of an FMA micro-benchmark on the current device."""
+    t, ms = ctypes.c_double(), ctypes.c_double()
+    _check(lib.spm_measure_peak(int(kind), ctypes.byref(t), ctypes.byref(ms)))
+    return t.value, ms.value
 
 
 def set_apply_plan(prec, L, zvariant):
@@ -112,6 +122,7 @@ def _load():
         "spm_batch_build_stencils": [P, I],
         "spm_batch_apply_A": [P, I, P, P, P],
         "spm_batch_solve": [P, I, P, P, D, I, I, P],
+        "spm_measure_peak": [I, ctypes.POINTER(D), ctypes.POINTER(D)],
     }
     for name, args in sig.items():
         f = getattr(L, name)

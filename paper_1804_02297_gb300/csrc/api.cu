@@ -85,7 +85,7 @@ extern "C" spm_status spm_create_problem(int n, double omega, const double *eps_
 {
     if (!out) { spm_set_error("out is NULL"); return SPM_ERR_INVALID_ARG; }
     *out = nullptr;
-    if (n < 4 || n > 512) { spm_set_error("n = %d outside [4, 512]", n); return SPM_ERR_INVALID_ARG; }
+    if (n < 4 || n > 256) { spm_set_error("n = %d outside [4, 256] (FFT lengths 2n up to 512)", n); return SPM_ERR_INVALID_ARG; }
     if ((n & (n - 1)) != 0 && n != 48 && n != 96) {
         spm_set_error("n = %d: the FFT length 2n must be a power of two or 96, 192 (n = 48, 96)", n);
         return SPM_ERR_INVALID_ARG;

@@ -566,10 +566,15 @@ __global__ void __launch_bounds__(tx_of<R, L>::v * L / line_elems(L)) k2_ztma(co
         if (threadIdx.x == 0 && tile + 2 * (int)gridDim.x < ntiles) issue(tile + 2 * gridDim.x, st);
     }
     if (failed && threadIdx.x == 0) {
-        atomicExch(err, 1);
-        // the other stage may still have a copy in flight: wait for it (bounded) before leaving
+        // Both stages may still have copies in flight: the one whose wait expired
+        // and the next one.  Wait for each (bounded) before the block leaves, so
+        // that no bulk copy writes into shared memory after the exit.  Code 1: the
+        // wait expired and both copies then landed; code 3: a copy was still
+        // outstanding after the second bounded wait (the exit is then best effort).
+        bool drained = mbar_wait(&bar[it & 1], (it >> 1) & 1);
         const int nxt = it + 1;
-        if ((int)(blockIdx.x + (unsigned)nxt * gridDim.x) < ntiles) mbar_wait(&bar[nxt & 1], (nxt >> 1) & 1);
+        if ((int)(blockIdx.x + (unsigned)nxt * gridDim.x) < ntiles) drained = mbar_wait(&bar[nxt & 1], (nxt >> 1) & 1) && drained;
+        atomicExch(err, drained ? 1 : 3);
     }
 }
 
@@ -844,17 +849,20 @@ spm_status apply_A_typed(spm_problem_s *P, const void *xv, void *yv, int nrhs, c
 //   (of 81) from the expanded table [cls][d][o][c] (zero outside the class
 //   neighbourhood, which is also where a neighbour would leave the grid) and
 //   the warp sums its partials;
-// * interior blocks (1 <= i_d <= n-2, one class): a 32 x 4 x 2 tile whose three
-//   components plus a one-point halo are staged in shared memory; the class's
-//   243 coefficients arrive as a by-value kernel parameter, so they sit in the
-//   constant bank and enter the FMAs as operands without load instructions.
+// * interior blocks (1 <= i_d <= n-2, one class): a 32 x 8 x QZ tile whose three
+//   components plus a one-point halo are staged in shared memory; each thread
+//   owns QZ = 4 points stacked along z, so every staged value it loads feeds the
+//   three z-offsets of up to three of its points (6 loads per (d, o1, o2) serve
+//   36 complex MACs per output component instead of one load per MAC); the
+//   class's 243 coefficients arrive as a by-value kernel parameter, so they sit
+//   in the constant bank, and each feeds QZ points once in registers.
 constexpr int Q_THREADS = 256;
-constexpr int QX = 32, QY = 4, QZ = 2;
+constexpr int QX = 32, QY = 8, QZ = 4;
 constexpr int QHX = QX + 2, QHY = QY + 2, QHZ = QZ + 2, QH = QHX * QHY * QHZ;
 constexpr int QF_U = 32, QF_W = 8;
 constexpr int QF_HU = QF_U + 2, QF_HW = QF_W + 2, QF_HALO = 3 * 2 * QF_HW * QF_HU;
 constexpr int Q_SMEM = (3 * QH > QF_HALO + 162) ? 3 * QH : QF_HALO + 162; // complex elements
-static_assert(QX * QY * QZ == Q_THREADS && QF_U * QF_W == Q_THREADS, "Q block shapes");
+static_assert(QX * QY == Q_THREADS && QF_U * QF_W == Q_THREADS, "Q block shapes");
 
 template <typename C> struct QInterior {
     C a[243]; // [d][o][c], o = (o3+1)*9 + (o2+1)*3 + (o1+1)
@@ -893,6 +901,7 @@ __device__ __forceinline__ void q_interior_block(int blk, const C *__restrict__ 
     const int tiles_x = (m + QX - 1) / QX, tiles_y = (m + QY - 1) / QY;
     const int txy = blk % (tiles_x * tiles_y), tz = blk / (tiles_x * tiles_y);
     const int tx0 = 1 + (txy % tiles_x) * QX, ty0 = 1 + (txy / tiles_x) * QY, tz0 = 1 + tz * QZ;
+    // halo [d][hz][hy][hx], x fastest: each warp's loads below read 32 consecutive x
     for (int i = threadIdx.x; i < 3 * QH; i += Q_THREADS) {
         int d = i / QH, h = i % QH;
         int hx = h % QHX, hy = (h / QHX) % QHY, hz = h / (QHX * QHY);
@@ -902,39 +911,60 @@ __device__ __forceinline__ void q_interior_block(int blk, const C *__restrict__ 
         sv[i] = val;
     }
     __syncthreads();
-    const int lx = threadIdx.x % QX, ly = (threadIdx.x / QX) % QY, lz = threadIdx.x / (QX * QY);
-    const int i1 = tx0 + lx, i2 = ty0 + ly, i3 = tz0 + lz;
-    if (i1 > n - 2 || i2 > n - 2 || i3 > n - 2) return;
-    C acc0 = czero<C>(), acc1 = czero<C>(), acc2 = czero<C>();
+    const int lx = threadIdx.x % QX, ly = threadIdx.x / QX;
+    const int i1 = tx0 + lx, i2 = ty0 + ly;
+    if (i1 > n - 2 || i2 > n - 2) return;
+    C acc[QZ][3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        int o = 0;
+    for (int q = 0; q < QZ; ++q) acc[q][0] = acc[q][1] = acc[q][2] = czero<C>();
 #pragma unroll
-        for (int o3 = -1; o3 <= 1; ++o3)
+    for (int d = 0; d < 3; ++d)
 #pragma unroll
-            for (int o2 = -1; o2 <= 1; ++o2)
+        for (int o2 = -1; o2 <= 1; ++o2)
 #pragma unroll
-                for (int o1 = -1; o1 <= 1; ++o1, ++o) {
-                    const int h = ((lz + 1 + o3) * QHY + (ly + 1 + o2)) * QHX + (lx + 1 + o1);
-                    if constexpr (std::is_same<C, float2>::value) {
-                        const float2 vv = sv[d * QH + h], vs = make_float2(vv.y, vv.x);
-                        const float4 a0 = qa.a[(d * 27 + o) * 3 + 0], a1 = qa.a[(d * 27 + o) * 3 + 1],
-                                     a2 = qa.a[(d * 27 + o) * 3 + 2];
-                        acc0 = __ffma2_rn(make_float2(a0.z, a0.w), vs, __ffma2_rn(make_float2(a0.x, a0.y), vv, acc0));
-                        acc1 = __ffma2_rn(make_float2(a1.z, a1.w), vs, __ffma2_rn(make_float2(a1.x, a1.y), vv, acc1));
-                        acc2 = __ffma2_rn(make_float2(a2.z, a2.w), vs, __ffma2_rn(make_float2(a2.x, a2.y), vv, acc2));
-                    } else {
-                        const C val = sv[d * QH + h];
-                        acc0 = cfma(qa.a[(d * 27 + o) * 3 + 0], val, acc0);
-                        acc1 = cfma(qa.a[(d * 27 + o) * 3 + 1], val, acc1);
-                        acc2 = cfma(qa.a[(d * 27 + o) * 3 + 2], val, acc2);
+            for (int o1 = -1; o1 <= 1; ++o1) {
+                // the z-column (d, i2 + o2, i1 + o1) over the tile's QZ + 2 halo planes
+                C col[QZ + 2];
+#pragma unroll
+                for (int j = 0; j < QZ + 2; ++j) col[j] = sv[d * QH + (j * QHY + ly + 1 + o2) * QHX + lx + 1 + o1];
+                if constexpr (std::is_same<C, float2>::value) {
+                    float2 cs[QZ + 2]; // (im, re) of each value, for the second packed FMA
+#pragma unroll
+                    for (int j = 0; j < QZ + 2; ++j) cs[j] = make_float2(col[j].y, col[j].x);
+#pragma unroll
+                    for (int o3 = -1; o3 <= 1; ++o3) {
+                        const int o = (o3 + 1) * 9 + (o2 + 1) * 3 + (o1 + 1);
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            const float4 a = qa.a[(d * 27 + o) * 3 + c];
+                            const float2 ar = make_float2(a.x, a.y), ai = make_float2(a.z, a.w);
+#pragma unroll
+                            for (int q = 0; q < QZ; ++q)
+                                acc[q][c] = __ffma2_rn(ai, cs[q + o3 + 1], __ffma2_rn(ar, col[q + o3 + 1], acc[q][c]));
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int o3 = -1; o3 <= 1; ++o3) {
+                        const int o = (o3 + 1) * 9 + (o2 + 1) * 3 + (o1 + 1);
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            const C a = qa.a[(d * 27 + o) * 3 + c];
+#pragma unroll
+                            for (int q = 0; q < QZ; ++q) acc[q][c] = cfma(a, col[q + o3 + 1], acc[q][c]);
+                        }
                     }
                 }
+            }
+#pragma unroll
+    for (int q = 0; q < QZ; ++q) {
+        const int i3 = tz0 + q;
+        if (i3 > n - 2) break;
+        const long i = ((long)i3 * n + i2) * n + i1;
+        yb[i] = acc[q][0];
+        yb[n3 + i] = acc[q][1];
+        yb[2 * n3 + i] = acc[q][2];
     }
-    const long i = ((long)i3 * n + i2) * n + i1;
-    yb[i] = acc0;
-    yb[n3 + i] = acc1;
-    yb[2 * n3 + i] = acc2;
 }
 
 template <typename C>
@@ -1053,7 +1083,8 @@ __global__ void __launch_bounds__(Q_THREADS) k_q(const typename cplx_of<R>::type
 {
     pdl_wait_and_trigger();
     using C = typename cplx_of<R>::type;
-    __shared__ C sv[Q_SMEM];
+    extern __shared__ unsigned char smem_raw[];
+    C *sv = reinterpret_cast<C *>(smem_raw); // Q_SMEM complex elements
     const long n3 = (long)n * n * n;
     const long b = blockIdx.y;
     const C *vb = v + b * 3 * n3;
@@ -1084,8 +1115,14 @@ spm_status apply_Q_typed(spm_problem_s *P, const void *vv, void *yv, int nrhs, c
     const int face_blocks = 6 * ((m + QF_U - 1) / QF_U) * ((m + QF_W - 1) / QF_W);
     const int nedge = 12 * m + 8;
     const int edge_blocks = (nedge + Q_THREADS / 32 - 1) / (Q_THREADS / 32);
-    launch_pdl(k_q<R>, dim3((unsigned)(face_blocks + edge_blocks + interior_blocks), (unsigned)nrhs), dim3(Q_THREADS), 0,
-               s, v, qa, qtab, y, n, face_blocks, edge_blocks, nedge);
+    constexpr size_t smem = sizeof(C) * Q_SMEM;
+    static bool attr = false;
+    if (!attr) {
+        allow_smem(k_q<R>, smem);
+        attr = true;
+    }
+    launch_pdl(k_q<R>, dim3((unsigned)(face_blocks + edge_blocks + interior_blocks), (unsigned)nrhs), dim3(Q_THREADS),
+               smem, s, v, qa, qtab, y, n, face_blocks, edge_blocks, nedge);
     SPM_CUDA_TRY(cudaGetLastError());
     return SPM_OK;
 }
@@ -1351,30 +1388,18 @@ spm_status spm_apply_init_attributes()
 static __device__ __align__(256) unsigned char g_spm_noalloc_scratch[SPM_NOALLOC_SCRATCH_BYTES];
 
 namespace {
-std::mutex g_noalloc_mu;
-void *g_noalloc_addr[128] = {}; // device address of the array, per device ordinal
-
 // Host code cannot use the array's name as a device address: look the address
-// up once per device, with that device current.
+// up on the current device.  The lookup is cheap and allocates nothing, so it is
+// repeated on every call (a cached address would go stale after a device reset).
 spm_status noalloc_scratch(void **out)
 {
-    int dev = 0;
-    SPM_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 128) {
-        spm_set_error("device ordinal %d out of range for the no-allocation scratch table", dev);
-        return SPM_ERR_INVALID_ARG;
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_spm_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        spm_set_error("cudaGetSymbolAddress of the no-allocation scratch failed: %s", cudaGetErrorString(e));
+        return SPM_ERR_CUDA;
     }
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_spm_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            spm_set_error("cudaGetSymbolAddress of the no-allocation scratch failed: %s", cudaGetErrorString(e));
-            return SPM_ERR_CUDA;
-        }
-        g_noalloc_addr[dev] = p;
-    }
-    *out = g_noalloc_addr[dev];
+    *out = p;
     return SPM_OK;
 }
 

@@ -123,6 +123,20 @@ def medium_gaussian(n: int, amplitude: float = 0.5, width: float = 0.15):
     return _bump_field(n, [(amplitude, width, (0.5, 0.5, 0.5))])
 
 
+def medium_gaussian_untapered(n: int, amplitude: float = 0.5, width: float = 0.08):
+    """Narrow centred Gaussian without the taper, eps = 1 + a exp(-|x-c|^2/(2 w^2)),
+    with its analytic gradient.  At w = 0.08 eps - 1 is below 3e-9 of its peak on
+    the boundary of the unit cube, and its derivatives stay moderate, so finite
+    differences of eps reach their asymptotic order already at n = 32."""
+    x, _ = grid_coords(n)
+    X3, X2, X1 = np.meshgrid(x, x, x, indexing="ij")
+    P = [X1, X2, X3]
+    r2 = sum((P[d] - 0.5) ** 2 for d in range(3))
+    e = amplitude * np.exp(-r2 / (2.0 * width * width))
+    grad = np.stack([-e * (P[d] - 0.5) / (width * width) for d in range(3)])
+    return (1.0 + e).astype(np.complex128), grad.astype(np.complex128)
+
+
 def draw_bumps(seed: int, count: int):
     rng = SplitMix64(seed)
     bumps = []

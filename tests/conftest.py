@@ -11,3 +11,25 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a) and the built library")
     config.addinivalue_line("markers", "slow: CPU test that takes tens of seconds")
+
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def read_paper_iteration_counts():
+    """Rows (medium, k/2pi, n, N_iter) of tests/golden/paper_iteration_counts.txt:
+    the preconditioned GMRES(20) iteration counts of the paper's 3-D Tables 4-6."""
+    rows = []
+    with open(os.path.join(GOLDEN, "paper_iteration_counts.txt")) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if not line:
+                continue
+            med, kk, n, it = line.split()
+            rows.append((med, float(kk), int(n), int(it)))
+    return rows
+
+
+@pytest.fixture(scope="session")
+def paper_iteration_counts():
+    return read_paper_iteration_counts()

@@ -367,9 +367,14 @@ def test_born_limit():
     assert 1.7 < ratios[0] / ratios[1] < 2.3
 
 
-def test_preconditioner_cuts_iterations():
-    """Behaviour (parity unpinned): S^{-1}Q-preconditioned GMRES needs few iterations
-    (the paper reports fewer than ten in every case; tests/golden/paper_iteration_counts.txt)."""
+def test_preconditioner_cuts_iterations(paper_iteration_counts):
+    """Behaviour (parity unpinned): S^{-1}Q-preconditioned GMRES needs few iterations.
+    The paper's 3-D tables (tests/golden/paper_iteration_counts.txt, Tables 4-6)
+    print 6 or 7 iterations for every medium and size, and the paper states that
+    every case needs fewer than ten; the oracle's count on a Gaussian lens must
+    respect that bound."""
+    counts = [r[3] for r in paper_iteration_counts]
+    assert len(counts) == 9 and min(counts) == 6 and max(counts) == 7
     n = 10
     k = si.wavenumber_for_grid(n)
     eps, grad = si.medium_gaussian(n)
@@ -382,7 +387,7 @@ def test_preconditioner_cuts_iterations():
     x0, it_0, rel_0, _ = oracle.gmres(n, k, m, p, g, tol=1e-6, restart=20, maxit=400)
     assert rel_p <= 1e-6
     assert it_p < it_0
-    assert it_p <= 12
+    assert it_p < 10
     # the preconditioned solution solves the original system too
     r = g - oracle.apply_fft(n, k, m, p, x)
     assert np.linalg.norm(r) / np.linalg.norm(g) < 1e-4
