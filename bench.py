@@ -123,7 +123,11 @@ def algorithmic_flops(n, op, nrhs=1):
 def zpass_name(spm, prec, L):
     """The z-pass kernel the library's timed plan chose for FFT length L."""
     z = spm.get_apply_plan(spm.SPM_C64 if prec == "c64" else spm.SPM_C128, L)
-    return {0: "four-line", 1: "one-field prefetch", 2: "TMA-fed persistent"}.get(z, "not chosen")
+    if z < 0:
+        return "not chosen"
+    name = {0: "four-line", 1: "one-field prefetch", 2: "TMA-fed persistent", 3: "16 per thread",
+            4: "staged spectra"}.get(z & 7, "?")
+    return name + (" + fused x/y plane passes" if z & 8 else "")
 
 
 def peaks():
@@ -513,6 +517,26 @@ def measure_solve(spm, torch, P, wl, args, have_c64_factor):
     return out
 
 
+def time_apply(torch, fn, x, y, steps, warmup=3):
+    """Median device time (ms) of fn(x, y) with the L2 flushed before each call."""
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(warmup):
+        fn(x, y)
+    torch.cuda.synchronize()
+    ev = []
+    for _ in range(steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn(x, y)
+        e1.record(stream)
+        ev.append((e0, e1))
+    torch.cuda.synchronize()
+    return float(np.median([a.elapsed_time(b) for a, b in ev]))
+
+
 def measure_n256(spm, torch, apk, hbm_peak, hbm_kind, steps=12, warmup=3):
     """The n = 256 apply of A (L = 512, 32 bumps, k = 64 pi, one right-hand side,
     complex64), where the pass intermediates (24 n^3 complex = 3.2 GB) stream
@@ -554,6 +578,9 @@ def measure_n256(spm, torch, apk, hbm_peak, hbm_kind, steps=12, warmup=3):
     if traffic is not None:
         out["dram_gbs"] = traffic / (ms / 1000.0) / 1e9
         out["dram_frac"] = out["dram_gbs"] / hbm_peak
+    # the cuFFT comparison apply (full padded 3-D transforms) on the same input
+    out["cufft_ms_per_apply"] = time_apply(torch, P.apply_A_cufft, x, y, steps)
+    out["ours_over_cufft_speedup"] = out["cufft_ms_per_apply"] / ms
     P.close()
     del P, x, y, flush
     torch.cuda.synchronize()
@@ -724,6 +751,12 @@ def run_ours(args):
             "gpu_launches": launches_per_step * args.steps * max(1, -(-nrhs // chunk_of(P, n, args.prec))),
             "clocks": clocks,
             "step_ms_min": float(np.min(step_ms)), "step_ms_median": float(np.median(step_ms))}
+    if args.prec == "c64" and nrhs == 1:
+        # the apply of A alone, hand-written passes against the cuFFT comparison apply
+        a_ms = time_apply(torch, P.apply_A, x, y, 200 if n <= 64 else 20)
+        c_ms = time_apply(torch, P.apply_A_cufft, x, y, 200 if n <= 64 else 20)
+        line["cufft_compare"] = {"op": "A", "n": n, "ours_ms": a_ms, "cufft_ms": c_ms, "speedup": c_ms / a_ms,
+                                 "note": "cuFFT: zero-padded (2n)^3 arrays, batched 3-D C2C plans, same product kernel"}
     if args.solve != "none" and n <= 64:
         line["solve"] = measure_solve(spm, torch, P, wl, args, True)
         line["solve"]["setup"] = setup

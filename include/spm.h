@@ -115,6 +115,18 @@ spm_status spm_apply_A(spm_problem prob, spm_prec prec, const void *x_dev, void 
 spm_status spm_apply_A_noalloc(spm_problem prob, spm_prec prec, const void *x_dev, void *y_dev,
                                int nrhs, void *stream);
 
+/* y = A x exactly as spm_apply_A, computed the textbook way through cuFFT:
+ * the four contrast-weighted fields zero-padded to full (2n)^3 arrays, one
+ * batched 3-D cuFFT forward transform, the Fourier-side product with the four
+ * kernel spectra, one batched inverse transform, crop and + x.  A comparison
+ * point for the hand-written passes of spm_apply_A (the paper has no such
+ * path; it states only that the convolutions are evaluated by FFT), not used
+ * by any other entry point.  The padded arrays (4 (2n)^3 complex values) and
+ * the cuFFT plans are allocated on first use and kept by the problem until
+ * spm_destroy; right-hand sides are processed one at a time. */
+spm_status spm_apply_A_cufft(spm_problem prob, spm_prec prec, const void *x_dev, void *y_dev,
+                             int nrhs, void *stream);
+
 /* y = Q A x: A as above followed by the sparsifying row combination Q,
  * (Q v)_{i,c} = sum_{(d,o) in tau(class i)} alpha_class[(d,o),c] v^d_{i+o}
  * (Eq. nbr_i_block_alpha; classes of Section 3.2).  Needs stencils
@@ -155,16 +167,20 @@ spm_status spm_set_stencils(spm_problem prob, const double *alpha_host, const do
 spm_status spm_get_stencils(spm_problem prob, double *alpha_host, double *beta_host, double *sv_host);
 
 /* Factor the assembled S (nested dissection, multifrontal LU on the device) in
- * `prec` (SPM_C128, SPM_C64 or SPM_C64H).  Pivoting stays inside each front, so
- * a box of the dissection whose part of S is nearly singular spoils the factor
- * even when S itself is well conditioned.  Two safeguards: pivots of a front
- * below 1e-8 (SPM_C128) or 1e-4 (complex64) times the front's largest pivot are
- * raised to that size (the factor is then exact for S plus a perturbation of
- * that rank); and the factor is probed:
+ * `prec` (SPM_C128, SPM_C64 or SPM_C64H).  Each front's fully summed block is
+ * inverted by the library's own Gauss-Jordan elimination with partial
+ * pivoting, and the Schur-complement products are the library's own complex
+ * GEMMs (no vendor dense library).  Pivoting stays inside each front, so a box
+ * of the dissection whose part of S is nearly singular spoils the factor even
+ * when S itself is well conditioned.  Two safeguards: pivots of a front below
+ * 1e-8 (SPM_C128) or 1e-4 (complex64) times the largest entry of its fully
+ * summed block are raised to that size (the factor is then exact for S plus a
+ * perturbation of that rank); and the factor is probed:
  * x = S^{-1} b for a fixed pseudo-random b, and the residual ||S x - b|| / ||b||
  * (S x in complex128) must be at most 1e-6 (SPM_C128), 3e-2 (SPM_C64) or 0.3
  * (SPM_C64H); otherwise up to three other trees (cut planes moved by one) are
- * factored and the most accurate factor is kept.  Synchronises. */
+ * factored and the most accurate factor is kept.  Synchronises.  SPM_ERR_TIMEOUT
+ * if a bounded wait between the blocks of the elimination kernel gave up. */
 spm_status spm_factor_S(spm_problem prob, spm_prec prec);
 
 /* Factor S on one tree variant (0 = cuts through the middle planes; 1, 2, 3 =
@@ -172,13 +188,6 @@ spm_status spm_factor_S(spm_problem prob, spm_prec prec);
  * retry; the probe residual is still recorded for spm_factor_info.
  * SPM_ERR_INVALID_ARG for a variant outside [0, 4). */
 spm_status spm_factor_S_tree(spm_problem prob, spm_prec prec, int variant);
-
-/* Process-wide GEMM mode of the complex64 factors built afterwards: 0 (the
- * default) runs the Schur-complement updates in FP32 on the CUDA cores, 1 lets
- * cuBLAS emulate FP32 on the BF16 tensor cores (BF16x9, FP32-level accuracy).
- * The probe of spm_factor_S checks either.  SPM_ERR_INVALID_ARG otherwise. */
-spm_status spm_set_factor_gemm(int mode);
-spm_status spm_get_factor_gemm(int *mode);
 
 /* Report on the current factor in `prec` (SPM_C128, or SPM_C64 / SPM_C64H for
  * the complex64 slot): tree variant kept (0 = middle cuts), factorisations run
@@ -210,11 +219,33 @@ spm_status spm_solve_S(spm_problem prob, spm_prec prec, const void *b_dev, void 
  *   1  one field at a time after a cp.async prefetch of all four (L >= 32, 96, 192),
  *   2  persistent, fed by TMA bulk-tensor copies into two shared-memory stages
  *      (L >= 32),
+ *   3  16 values per thread (one shared-memory exchange per line at L = 128
+ *      and 256), twiddles in registers, all four fields prefetched by cp.async
+ *      (L = 128, 256, 512),
+ *   4  as 1, with the tile's kernel spectra and the twiddle table also staged
+ *      in shared memory by cp.async (L >= 32),
  *  -1  not chosen yet: the next apply of that length times the candidates on
  *      its own data (outside stream capture) and keeps the fastest.
+ * Plus 8 (L = 64, 128 only): the x- and y-passes of each z-plane run fused in
+ * one kernel per direction (the plane's n x L intermediate stays in shared
+ * memory); the timing tries it with the fastest z-pass kernel.
  * SPM_ERR_INVALID_ARG for an unknown length or a variant the length lacks. */
 spm_status spm_get_apply_plan(spm_prec prec, int L, int *zvariant);
 spm_status spm_set_apply_plan(spm_prec prec, int L, int zvariant);
+
+/* The autotuner's choices persisted as JSON: {"device": name, "plans": [{"prec":
+ * "c64" | "c128", "L": length, "variant": v, "ms": [per-apply ms of variants
+ * 0..4 when they were timed, else 0], "fused_xy_ms": ms of the best variant with
+ * fused x and y passes, else 0}, ...]} for every (precision, length) whose
+ * variant is set.  spm_load_apply_plans installs the entries of a file written
+ * on a device of the same name (SPM_ERR_INVALID_ARG for another device or an
+ * unreadable file); *loaded (may be NULL) receives the number installed.  The
+ * first spm_create_problem of a process loads the file named by the
+ * environment variable SPM_APPLY_PLANS, if set (a file for another device is
+ * ignored).  The paper has no counterpart: this only fixes which of the
+ * equivalent kernels runs. */
+spm_status spm_save_apply_plans(const char *path);
+spm_status spm_load_apply_plans(const char *path, int *loaded);
 
 /* Synchronise the device and report whether any kernel of this problem gave up
  * a bounded wait since the last call (SPM_ERR_TIMEOUT, then cleared): the

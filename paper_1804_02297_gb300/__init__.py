@@ -23,15 +23,17 @@ SPM_C128, SPM_C64, SPM_MIXED, SPM_C64H = 0, 1, 2, 3
 # every symbol include/spm.h declares
 EXPORTS = [
     "spm_create_problem", "spm_destroy", "spm_problem_info", "spm_apply_A", "spm_apply_QA", "spm_apply_Q",
-    "spm_build_stencils", "spm_set_stencils", "spm_get_stencils", "spm_factor_S", "spm_factor_S_tree", "spm_factor_info", "spm_device_status", "spm_selftest_bounded_wait", "spm_set_factor_gemm", "spm_get_factor_gemm", "spm_get_apply_plan", "spm_set_apply_plan", "spm_apply_S",
+    "spm_build_stencils", "spm_set_stencils", "spm_get_stencils", "spm_factor_S", "spm_factor_S_tree", "spm_factor_info", "spm_device_status", "spm_selftest_bounded_wait", "spm_get_apply_plan", "spm_set_apply_plan", "spm_apply_S",
     "spm_solve_S", "spm_incident_plane_wave", "spm_rhs_from_incident", "spm_solve", "spm_kernel_entries",
     "spm_lattice_constant", "spm_last_error", "spm_apply_A_noalloc",
     "spm_create_batch", "spm_destroy_batch", "spm_batch_size", "spm_batch_problem", "spm_batch_build_stencils",
-    "spm_batch_apply_A", "spm_batch_solve", "spm_measure_peak",
+    "spm_batch_apply_A", "spm_batch_solve", "spm_measure_peak", "spm_apply_A_cufft",
+    "spm_save_apply_plans", "spm_load_apply_plans",
 ]
 
 
-ZPASS_FOUR, ZPASS_ONE, ZPASS_TMA = 0, 1, 2
+ZPASS_FOUR, ZPASS_ONE, ZPASS_TMA, ZPASS_E16, ZPASS_STAGED = 0, 1, 2, 3, 4
+PLAN_FUSED_XY = 8  # add to a z-pass variant: x and y passes fused per z-plane (L = 64, 128)
 
 
 def get_apply_plan(prec, L):
@@ -41,15 +43,16 @@ def get_apply_plan(prec, L):
     return z.value
 
 
-def set_factor_gemm(mode):
-    """GEMM mode of complex64 factors built afterwards: 0 FP32, 1 BF16x9-emulated FP32."""
-    _check(lib.spm_set_factor_gemm(int(mode)))
+def save_apply_plans(path):
+    """Write the autotuned apply plans (and the candidate timings) as JSON."""
+    _check(lib.spm_save_apply_plans(os.fsencode(path)))
 
 
-def get_factor_gemm():
-    m = ctypes.c_int()
-    _check(lib.spm_get_factor_gemm(ctypes.byref(m)))
-    return m.value
+def load_apply_plans(path):
+    """Install the plans of a JSON file written on this kind of device; returns the count."""
+    k = ctypes.c_int()
+    _check(lib.spm_load_apply_plans(os.fsencode(path), ctypes.byref(k)))
+    return k.value
 
 
 PEAK_FFMA, PEAK_FFMA2, PEAK_DFMA = 0, 1, 2
@@ -95,6 +98,9 @@ def _load():
         "spm_problem_info": [P, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(ctypes.c_longlong)],
         "spm_apply_A": [P, I, P, P, I, P],
         "spm_apply_A_noalloc": [P, I, P, P, I, P],
+        "spm_apply_A_cufft": [P, I, P, P, I, P],
+        "spm_save_apply_plans": [ctypes.c_char_p],
+        "spm_load_apply_plans": [ctypes.c_char_p, ctypes.POINTER(I)],
         "spm_apply_QA": [P, I, P, P, I, P],
         "spm_apply_Q": [P, I, P, P, I, P],
         "spm_build_stencils": [P, I],
@@ -105,8 +111,6 @@ def _load():
         "spm_factor_S_tree": [P, I, I],
         "spm_device_status": [P],
         "spm_selftest_bounded_wait": [P],
-        "spm_set_factor_gemm": [I],
-        "spm_get_factor_gemm": [ctypes.POINTER(I)],
         "spm_get_apply_plan": [I, I, ctypes.POINTER(I)],
         "spm_set_apply_plan": [I, I, I],
         "spm_apply_S": [P, I, P, P, I, P],
@@ -233,6 +237,11 @@ class Problem:
     def apply_A_noalloc(self, x, y, stream=None):
         """y = A x with no device allocation in the call (fixed library scratch)."""
         _check(lib.spm_apply_A_noalloc(self.h, _prec_of(x), _ptr(x), _ptr(y), _nrhs(x, self.n), _stream(stream)))
+        return y
+
+    def apply_A_cufft(self, x, y, stream=None):
+        """y = A x through cuFFT 3-D transforms (comparison path, not the hot path)."""
+        _check(lib.spm_apply_A_cufft(self.h, _prec_of(x), _ptr(x), _ptr(y), _nrhs(x, self.n), _stream(stream)))
         return y
 
     def apply_QA(self, x, y, stream=None):

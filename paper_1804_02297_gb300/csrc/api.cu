@@ -1,6 +1,7 @@
 // C-ABI entry points of libspm (include/spm.h): argument checks, problem
 // set-up on the host (medium, twiddles, lattice constant) and dispatch.
 #include <math.h>
+#include <stdlib.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -97,6 +98,12 @@ extern "C" spm_status spm_create_problem(int n, double omega, const double *eps_
     if (!attrs) {
         SPM_TRY(spm_apply_init_attributes());
         attrs = true;
+        // apply plans tuned earlier on this kind of device, if the caller names a file
+        const char *plans = getenv("SPM_APPLY_PLANS");
+        if (plans && *plans) {
+            int loaded = 0;
+            if (spm_load_plans_impl(plans, &loaded) != SPM_OK) spm_set_error(""); // a stale or foreign file is ignored
+        }
     }
 
     spm_problem_s *P = new spm_problem_s();
@@ -212,6 +219,7 @@ extern "C" spm_status spm_destroy(spm_problem P)
     P->S128.release(); P->S64.release(); P->kry.release(); P->gmres_ws.release(); P->dev_err.release();
     spm_factor_free(P->fac128);
     spm_factor_free(P->fac64);
+    spm_cufft_free(P->cufft);
     delete P;
     return SPM_OK;
 }
@@ -327,18 +335,16 @@ extern "C" spm_status spm_set_apply_plan(spm_prec prec, int L, int zvariant)
     return spm_apply_plan_impl(prec, L, nullptr, &zvariant);
 }
 
-extern "C" spm_status spm_set_factor_gemm(int mode)
+extern "C" spm_status spm_save_apply_plans(const char *path)
 {
-    if (mode != 0 && mode != 1) { spm_set_error("factor GEMM mode must be 0 (FP32) or 1 (BF16x9-emulated FP32)"); return SPM_ERR_INVALID_ARG; }
-    spm_set_factor_gemm_mode(mode);
-    return SPM_OK;
+    if (!path) { spm_set_error("NULL path"); return SPM_ERR_INVALID_ARG; }
+    return spm_save_plans_impl(path);
 }
 
-extern "C" spm_status spm_get_factor_gemm(int *mode)
+extern "C" spm_status spm_load_apply_plans(const char *path, int *loaded)
 {
-    if (!mode) { spm_set_error("NULL argument"); return SPM_ERR_INVALID_ARG; }
-    *mode = spm_factor_gemm_mode();
-    return SPM_OK;
+    if (!path) { spm_set_error("NULL path"); return SPM_ERR_INVALID_ARG; }
+    return spm_load_plans_impl(path, loaded);
 }
 
 extern "C" spm_status spm_selftest_bounded_wait(spm_problem P)

@@ -18,11 +18,15 @@
 #include <cuda.h> // CUtensorMap (the encoder is reached through the runtime, no libcuda link)
 
 #include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <string>
 #include <mutex>
 #include <type_traits>
 #include <vector>
 
 #include "fft.cuh"
+#include "fft16.cuh"
 #include "fft_reg.cuh"
 
 namespace {
@@ -76,7 +80,8 @@ template <typename R, int L> struct tx_of {
     static constexpr int v = w < L ? w : L; // never wider than a row of L elements
 };
 
-constexpr int ZPROD_FOUR = 0, ZPROD_ONE = 1, ZPROD_TMA = 2; // z-pass kernel choices
+constexpr int ZPROD_FOUR = 0, ZPROD_ONE = 1, ZPROD_TMA = 2, ZPROD_E16 = 3, ZPROD_STAGED = 4; // z-pass kernel choices
+constexpr int ZPLAN_FUSED_XY = 8; // plan bit: x and y passes fused per z-plane (L = 64, 128)
 
 template <int L> __device__ __forceinline__ int xpad(int pos) { return pos + (pos >> 3); }
 
@@ -85,6 +90,13 @@ template <int BYTES> __device__ __forceinline__ void cp_async(void *smem, const 
 {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(BYTES) : "memory");
+}
+// the same with zero fill: when !valid no byte is read and the BYTES of smem are zeroed
+template <int BYTES> __device__ __forceinline__ void cp_async_zfill(void *smem, const void *gmem, bool valid)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(sa), "l"(gmem), "n"(BYTES), "r"(valid ? BYTES : 0)
+                 : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
@@ -326,6 +338,110 @@ __global__ void __launch_bounds__(tx_of<R, L>::v * L / line_elems(L)) k2_zprod1(
     }
 }
 
+// zprod, staged: as k2_zprod1 (the four fields' columns prefetched with
+// cp.async, one field transformed at a time), and also the tile's kernel
+// spectra and the twiddle table staged in shared memory, so that no global load
+// remains between the transforms.  The tile's spectra: for each kernel K and
+// folded z-frequency a3 in [0, n], the TX values at the tile's folded (a2, a1)
+// (ks[K][a3][c]); K(zeta) and K(L - zeta) share the entry (with the sign of K_3
+// flipped), so n + 1 rows cover all L frequencies.
+template <typename R, int L> struct zst {
+    using C = typename cplx_of<R>::type;
+    static constexpr int TX = tx_of<R, L>::v, n = L / 2, THREADS = TX * L / line_elems(L);
+    static constexpr size_t elems = (size_t)L * TX + 4 * n * TX + 4 * (n + 1) * TX + L;
+    static constexpr size_t smem = sizeof(C) * elems;
+};
+
+template <typename R, int L>
+__global__ void __launch_bounds__(zst<R, L>::THREADS) k2_zstaged(typename cplx_of<R>::type *W2,
+                                                                const typename cplx_of<R>::type *__restrict__ spec,
+                                                                const typename cplx_of<R>::type *__restrict__ tw)
+{
+    pdl_wait_and_trigger();
+    using C = typename cplx_of<R>::type;
+    constexpr int E = line_elems(L), H = E / 2;
+    constexpr int T = L / E, TX = tx_of<R, L>::v, n = L / 2, n1 = n + 1, THR = zst<R, L>::THREADS;
+    constexpr long L2 = (long)L * L, oct = (long)n1 * n1 * n1, fs = (long)n * L * L;
+    extern __shared__ unsigned char smem_raw[];
+    C *sm = reinterpret_cast<C *>(smem_raw); // exchange [L][TX]
+    C *pre = sm + L * TX;                    // [4 fields in consumption order][n][TX]
+    C *ks = pre + 4 * n * TX;                // [4 kernels][n + 1][TX]
+    C *stw = ks + 4 * n1 * TX;               // [L] twiddles
+    const int c = threadIdx.x % TX, t = threadIdx.x / TX;
+    const long col0 = (long)blockIdx.x * TX, col = col0 + c;
+    const int b = blockIdx.y;
+    C *base = W2 + (long)b * 4 * fs + col;
+    const int eta = (int)(col / L), xi = (int)(col % L);
+    const int a1 = xi <= n ? xi : L - xi, a2 = eta <= n ? eta : L - eta;
+    // group 0: p.E (consumed first)
+#pragma unroll
+    for (int q = 0; q < H; ++q) {
+        const int z = t + T * q;
+        cp_async<sizeof(C)>(&pre[z * TX + c], base + 3 * fs + (long)z * L2);
+    }
+    cp_async_commit();
+    // group 1: the tile's spectra (every thread copies a share; read after a barrier)
+    {
+        const int xi0 = (int)(col0 % L);
+        for (int i = threadIdx.x; i < 4 * n1 * TX; i += THR) {
+            const int k = i / (n1 * TX), a3 = (i / TX) % n1, cc = i % TX;
+            const int x = xi0 + cc, b1 = x <= n ? x : L - x;
+            cp_async<sizeof(C)>(&ks[i], spec + k * oct + ((long)a3 * n1 + a2) * n1 + b1);
+        }
+    }
+    cp_async_commit();
+    // groups 2..4: E^1, E^2, E^3
+#pragma unroll
+    for (int g = 1; g < 4; ++g) {
+#pragma unroll
+        for (int q = 0; q < H; ++q) {
+            const int z = t + T * q;
+            cp_async<sizeof(C)>(&pre[(g * n + z) * TX + c], base + (g - 1) * fs + (long)z * L2);
+        }
+        cp_async_commit();
+    }
+    for (int i = threadIdx.x; i < L; i += THR) stw[i] = tw[i];
+    auto buf = [&](int pos) -> C & { return sm[pos * TX + c]; };
+    auto sync = [&]() { __syncthreads(); };
+    C w4[E];
+    cp_async_wait<4>();
+#pragma unroll
+    for (int q = 0; q < H; ++q) w4[q] = pre[(t + T * q) * TX + c];
+#pragma unroll
+    for (int q = H; q < E; ++q) w4[q] = czero<C>();
+    __syncthreads(); // the twiddle table
+    line_fft<-1, L, true>(w4, t, buf, sync, stw);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        C v[E];
+        // this thread's copies of E^(d+1) and of the spectra have landed; the
+        // barriers inside the forward transform below make every thread's
+        // spectrum copies visible before the product reads them
+        if (d == 0) cp_async_wait<2>();
+        else if (d == 1) cp_async_wait<1>();
+        else cp_async_wait<0>();
+#pragma unroll
+        for (int q = 0; q < H; ++q) v[q] = pre[((d + 1) * n + t + T * q) * TX + c];
+#pragma unroll
+        for (int q = H; q < E; ++q) v[q] = czero<C>();
+        line_fft<-1, L, true>(v, t, buf, sync, stw);
+        const int fr_fixed = d == 0 ? xi : eta;
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+            const int zeta = t + T * q;
+            const int a3 = zeta <= n ? zeta : L - zeta;
+            const C K0 = ks[a3 * TX + c];
+            C Kd = ks[((1 + d) * n1 + a3) * TX + c];
+            const int fr = d == 2 ? zeta : fr_fixed;
+            if (fr > n) { Kd.x = -Kd.x; Kd.y = -Kd.y; }
+            v[q] = cfma(K0, v[q], cmul(Kd, w4[q]));
+        }
+        line_fft<1, L, false>(v, t, buf, sync, stw);
+#pragma unroll
+        for (int q = 0; q < H; ++q) base[d * fs + (long)(t + T * q) * L2] = v[q];
+    }
+}
+
 // zprod, E = 8: the four forward z-transforms run together (shared barriers),
 // then the three products and the three inverse transforms together.
 template <typename R, int L>
@@ -376,6 +492,236 @@ __global__ void __launch_bounds__(tx_of<R, L>::v * L / 8) k2_zprod4(typename cpl
     for (int d = 0; d < 3; ++d)
 #pragma unroll
         for (int q = 0; q < 4; ++q) base[d * fs + (long)(t + T * q) * L2] = v[d][q];
+}
+
+// Exchange buffer of a 16-per-thread line shared by TX columns: position pos of
+// column c at (pos + pos/16) TX + c.  The pad of one row per 16 positions keeps
+// the stage-0 writes (positions 16 t + q) of the T threads of a half-warp on
+// distinct banks when TX < 16.
+template <int L> __host__ __device__ constexpr int xch16_rows() { return L + L / 16; }
+__device__ __forceinline__ int xch16(int pos, int TX, int c) { return (pos + (pos >> 4)) * TX + c; }
+
+template <typename R, int L> struct zp16 {
+    // 128 threads (complex64) or 64 (complex128) per block: TX columns x L/16
+    static constexpr int TX = (sizeof(R) == 4 ? 16 : 8) * 128 / L;
+    static constexpr int THREADS = TX * (L / 16);
+    // blocks per SM the register budget is sized for: about 168 registers a thread
+    // in complex64, 255 in complex128
+    static constexpr int MINB = 65536 / (THREADS * (sizeof(R) == 4 ? 168 : 255));
+    static constexpr size_t smem()
+    {
+        using C = typename cplx_of<R>::type;
+        return sizeof(C) * ((size_t)(xch16_rows<L>() + L) * TX + 4 * (L / 2) * TX + (L == 512 ? L : 0));
+    }
+};
+
+// z-pass with 16 values per thread (fft16.cuh; L = 128, 256, 512): TX adjacent
+// columns per block, the four fields' columns (pruned half) prefetched into
+// shared memory with cp.async in consumption order (p.E first), the middle
+// stage's twiddles computed once per thread and kept in registers, p.E
+// transformed once and kept in registers, then per d: forward transform,
+// Fourier-side product, inverse transform, z < n stored in place.
+template <typename R, int L>
+__global__ void __launch_bounds__(zp16<R, L>::THREADS, zp16<R, L>::MINB) k3_zpass(typename cplx_of<R>::type *W2,
+                                                              const typename cplx_of<R>::type *__restrict__ spec,
+                                                              const typename cplx_of<R>::type *__restrict__ tw)
+{
+    pdl_wait_and_trigger();
+    using C = typename cplx_of<R>::type;
+    constexpr int T = L / 16, TX = zp16<R, L>::TX, n = L / 2, n1 = n + 1;
+    constexpr long L2 = (long)L * L, oct = (long)n1 * n1 * n1, fs = (long)n * L * L;
+    extern __shared__ unsigned char smem_raw[];
+    C *xch = reinterpret_cast<C *>(smem_raw); // exchange buffer [L + L/16][TX]
+    C *w4s = xch + xch16_rows<L>() * TX;      // transformed p.E [L][TX]
+    C *pre = w4s + L * TX;                    // [4 fields in consumption order][n][TX]
+    C *stw = pre + 4 * n * TX;                // [L] forward twiddles (L = 512)
+    const int c = threadIdx.x % TX, t = threadIdx.x / TX;
+    const long col = (long)blockIdx.x * TX + c;
+    const int b = blockIdx.y;
+    C *base = W2 + (long)b * 4 * fs + col;
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        const int f = g == 0 ? 3 : g - 1;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int z = t + T * q;
+            cp_async<sizeof(C)>(&pre[(g * n + z) * TX + c], base + f * fs + (long)z * L2);
+        }
+        cp_async_commit();
+    }
+    if constexpr (L == 512) {
+        for (int i = threadIdx.x; i < L; i += blockDim.x) stw[i] = tw[i];
+        __syncthreads();
+    }
+    fft16::Tw16<C, L> twr;
+    twr.init(t, tw);
+    const int eta = (int)(col / L), xi = (int)(col % L);
+    const int a1 = xi <= n ? xi : L - xi, a2 = eta <= n ? eta : L - eta;
+    auto buf = [&](int pos) -> C & { return xch[xch16(pos, TX, c)]; };
+    auto sync = [&]() { __syncthreads(); };
+    {
+        C w4[16];
+        cp_async_wait<3>();
+#pragma unroll
+        for (int q = 0; q < 8; ++q) w4[q] = pre[(t + T * q) * TX + c];
+#pragma unroll
+        for (int q = 8; q < 16; ++q) w4[q] = czero<C>();
+        fft16::line<-1, L, true>(w4, t, buf, sync, twr, stw);
+        // kept in shared memory; each thread reads back only its own positions
+#pragma unroll
+        for (int q = 0; q < 16; ++q) w4s[(t + T * q) * TX + c] = w4[q];
+    }
+    cp_async_wait<0>(); // the other three fields (copies of this thread's own elements)
+#pragma unroll 1
+    for (int d = 0; d < 3; ++d) {
+        C v[16];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = pre[((d + 1) * n + t + T * q) * TX + c];
+#pragma unroll
+        for (int q = 8; q < 16; ++q) v[q] = czero<C>();
+        fft16::line<-1, L, true>(v, t, buf, sync, twr, stw);
+        const int fr_fixed = d == 0 ? xi : eta;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            const int zeta = t + T * q;
+            const int a3 = zeta <= n ? zeta : L - zeta;
+            const long o = ((long)a3 * n1 + a2) * n1 + a1;
+            C K0 = spec[o], Kd = spec[(1 + d) * oct + o];
+            const int fr = d == 2 ? zeta : fr_fixed;
+            if (fr > n) { Kd.x = -Kd.x; Kd.y = -Kd.y; }
+            v[q] = cfma(K0, v[q], cmul(Kd, w4s[(t + T * q) * TX + c]));
+        }
+        fft16::line<1, L, false>(v, t, buf, sync, twr, stw);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) base[d * fs + (long)(t + T * q) * L2] = v[q];
+    }
+}
+
+// Fused x and y passes of one z-plane (lengths with 8 values per thread,
+// L <= 128): the plane's n x L intermediate stays in shared memory instead of
+// going through W1.
+//   k2_xyfwd, block (z, f, b): the x-transforms of the plane's n rows of w_f
+//     (formed on the fly), kept in S[y][xi]; then the y-transforms of its L
+//     columns (n nonzero inputs), written to W2[b][f][z][eta][xi].
+//   k2_yxinv, block (z, d, b): the inverse y-transforms of the L columns of
+//     W2[b][d][z], rows eta < n kept in S; then the inverse x-transforms of the n
+//     rows, x < n kept, plus the identity term: y[b][d][z][y][x].
+// 256 threads: LPR = 256 / (L/8) lines per round.  S rows are padded like the
+// row passes (xpad), columns go through a separate [L][LPR] exchange buffer.
+template <typename R, int L> struct xyf {
+    using C = typename cplx_of<R>::type;
+    static constexpr int n = L / 2, T = L / 8, LPR = 256 / T, LS = L + L / 8;
+    static constexpr size_t smem = sizeof(C) * ((size_t)n * LS + (size_t)L * LPR);
+    static_assert(L == 64 || L == 128, "fused plane passes: L = 64 or 128");
+    static_assert(n % LPR == 0 && L % LPR == 0, "whole rounds of lines");
+};
+
+template <typename R, int L>
+__global__ void __launch_bounds__(256) k2_xyfwd(const typename cplx_of<R>::type *__restrict__ x,
+                                                const typename cplx_of<R>::type *__restrict__ m,
+                                                const typename cplx_of<R>::type *__restrict__ p,
+                                                typename cplx_of<R>::type *__restrict__ W2,
+                                                const typename cplx_of<R>::type *__restrict__ tw)
+{
+    pdl_wait_and_trigger();
+    using C = typename cplx_of<R>::type;
+    constexpr int n = xyf<R, L>::n, T = xyf<R, L>::T, LPR = xyf<R, L>::LPR, LS = xyf<R, L>::LS;
+    constexpr long n2 = (long)n * n, n3 = n2 * n, L2 = (long)L * L;
+    extern __shared__ unsigned char smem_raw[];
+    C *S = reinterpret_cast<C *>(smem_raw); // [n][LS]
+    C *X = S + n * LS;                      // [L][LPR]
+    const int z = blockIdx.x, f = blockIdx.y, b = blockIdx.z;
+    const C *xb = x + (long)b * 3 * n3;
+    auto sync = [&]() { __syncthreads(); };
+    {   // x-transforms of the rows
+        const int line = threadIdx.x / T, t = threadIdx.x % T;
+        for (int y0 = 0; y0 < n; y0 += LPR) {
+            const int y = y0 + line;
+            C v[8];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const long off = ((long)z * n + y) * n + t + T * q;
+                v[q] = f < 3 ? cmul(m[off], xb[f * n3 + off])
+                             : cfma(p[off], xb[off], cfma(p[n3 + off], xb[n3 + off], cmul(p[2 * n3 + off], xb[2 * n3 + off])));
+                v[q + 4] = czero<C>();
+            }
+            C *row = S + y * LS; // the row's slot is also its exchange buffer
+            auto buf = [&](int pos) -> C & { return row[xpad<L>(pos)]; };
+            fftr::fft_line<-1, L, true>(v, t, buf, sync, tw);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) row[xpad<L>(t + T * q)] = v[q];
+        }
+        __syncthreads();
+    }
+    {   // y-transforms of the columns
+        const int c = threadIdx.x % LPR, t = threadIdx.x / LPR;
+        auto buf = [&](int pos) -> C & { return X[pos * LPR + c]; };
+        C *dst = W2 + (((long)b * 4 + f) * n + z) * L2;
+        for (int xi0 = 0; xi0 < L; xi0 += LPR) {
+            const int xi = xi0 + c;
+            C v[8];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] = S[(t + T * q) * LS + xpad<L>(xi)];
+#pragma unroll
+            for (int q = 4; q < 8; ++q) v[q] = czero<C>();
+            fftr::fft_line<-1, L, true>(v, t, buf, sync, tw);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) dst[(long)(t + T * q) * L + xi] = v[q];
+        }
+    }
+}
+
+template <typename R, int L>
+__global__ void __launch_bounds__(256) k2_yxinv(const typename cplx_of<R>::type *__restrict__ W2,
+                                                const typename cplx_of<R>::type *__restrict__ xin,
+                                                typename cplx_of<R>::type *__restrict__ y,
+                                                const typename cplx_of<R>::type *__restrict__ tw)
+{
+    pdl_wait_and_trigger();
+    using C = typename cplx_of<R>::type;
+    constexpr int n = xyf<R, L>::n, T = xyf<R, L>::T, LPR = xyf<R, L>::LPR, LS = xyf<R, L>::LS;
+    constexpr long n2 = (long)n * n, n3 = n2 * n, L2 = (long)L * L;
+    extern __shared__ unsigned char smem_raw[];
+    C *S = reinterpret_cast<C *>(smem_raw); // [n][LS]
+    C *X = S + n * LS;                      // [L][LPR]
+    const int z = blockIdx.x, d = blockIdx.y, b = blockIdx.z;
+    auto sync = [&]() { __syncthreads(); };
+    {   // inverse y-transforms of the columns, eta < n kept
+        const int c = threadIdx.x % LPR, t = threadIdx.x / LPR;
+        auto buf = [&](int pos) -> C & { return X[pos * LPR + c]; };
+        const C *src = W2 + (((long)b * 4 + d) * n + z) * L2;
+        for (int xi0 = 0; xi0 < L; xi0 += LPR) {
+            const int xi = xi0 + c;
+            C v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = src[(long)(t + T * q) * L + xi];
+            fftr::fft_line<1, L, false>(v, t, buf, sync, tw);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) S[(t + T * q) * LS + xpad<L>(xi)] = v[q];
+        }
+    }
+    __syncthreads();
+    {   // inverse x-transforms of the rows, x < n kept, + x
+        const int line = threadIdx.x / T, t = threadIdx.x % T;
+        const C *xb = xin + ((long)b * 3 + d) * n3;
+        C *yb = y + ((long)b * 3 + d) * n3;
+        for (int y0 = 0; y0 < n; y0 += LPR) {
+            const int yy = y0 + line;
+            C *row = S + yy * LS;
+            C v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = row[xpad<L>(t + T * q)];
+            C xi[4];
+            const long off = ((long)z * n + yy) * n;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) xi[q] = xb[off + t + T * q];
+            __syncthreads(); // the rows are in registers before they serve as exchange buffers
+            auto buf = [&](int pos) -> C & { return row[xpad<L>(pos)]; };
+            fftr::fft_line<1, L, false>(v, t, buf, sync, tw);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) yb[off + t + T * q] = xi[q] + v[q];
+        }
+    }
 }
 
 // xinv: rows of V1 (length L) -> y = x + IFFT(row)[x < n]
@@ -653,6 +999,8 @@ spm_status apply_chunk_v2(const typename cplx_of<R>::type *xb, typename cplx_of<
     constexpr int n = L / 2, T = L / line_elems(L), TX = tx_of<R, L>::v;
     constexpr int LPB = 256 / T > 0 ? 256 / T : 1;
     constexpr size_t sm_rows = sizeof(C) * LPB * (L + L / 8), sm_cols = sizeof(C) * L * TX;
+    const bool fused = (zvar & ZPLAN_FUSED_XY) != 0; // x and y passes fused per z-plane
+    zvar &= ZPLAN_FUSED_XY - 1;
     constexpr size_t sm_zprod = sm_cols + sizeof(C) * 4 * n * TX;
     constexpr size_t sm_zprod4 = 4 * sm_cols;
     static bool attrs = false;
@@ -671,21 +1019,59 @@ spm_status apply_chunk_v2(const typename cplx_of<R>::type *xb, typename cplx_of<
     }
     const long n2 = (long)n * n, L2 = (long)L * L;
     const int THR = TX * T; // threads of a strided-pass block
-    {
+    bool fused_done = false;
+    if constexpr (L == 64 || L == 128) {
+        if (fused) {
+            static bool axy = false;
+            if (!axy) {
+                allow_smem(k2_xyfwd<R, L>, xyf<R, L>::smem);
+                allow_smem(k2_yxinv<R, L>, xyf<R, L>::smem);
+                axy = true;
+            }
+            launch_pdl(k2_xyfwd<R, L>, dim3(n, 4, nb), dim3(256), xyf<R, L>::smem, s, xb, m, p, W2, tw);
+            fused_done = true;
+        }
+    }
+    if (!fused_done) {
         long rows = (long)nb * n2;
         launch_pdl(k2_xfwd<R, L>, dim3((unsigned)((rows + LPB - 1) / LPB)), dim3(LPB * T), sm_rows, s, xb, m, p, W1,
                    (int)rows, tw);
+        if constexpr (line_elems(L) == 8 && n % 2 == 0)
+            launch_pdl(k2_cols2<R, L, -1, true>, dim3(L / TX, n / 2, nb * 4), dim3(THR), 2 * sm_cols, s, (const C *)W1,
+                       W2, L, (long)L, 4, 4 * n2 * L, n2 * L, n * (long)L, 4 * (long)n * L2, (long)n * L2, L2, tw);
+        else
+            launch_pdl(k2_cols<R, L, -1, true>, dim3(L / TX, n, nb * 4), dim3(THR), sm_cols, s, (const C *)W1, W2, L,
+                       (long)L, 4, 4 * n2 * L, n2 * L, n * (long)L, 4 * (long)n * L2, (long)n * L2, L2, tw);
     }
-    if constexpr (line_elems(L) == 8 && n % 2 == 0)
-        launch_pdl(k2_cols2<R, L, -1, true>, dim3(L / TX, n / 2, nb * 4), dim3(THR), 2 * sm_cols, s, (const C *)W1, W2,
-                   L, (long)L, 4, 4 * n2 * L, n2 * L, n * (long)L, 4 * (long)n * L2, (long)n * L2, L2, tw);
-    else
-        launch_pdl(k2_cols<R, L, -1, true>, dim3(L / TX, n, nb * 4), dim3(THR), sm_cols, s, (const C *)W1, W2, L,
-                   (long)L, 4, 4 * n2 * L, n2 * L, n * (long)L, 4 * (long)n * L2, (long)n * L2, L2, tw);
     bool done = false;
     if constexpr (L >= 32) {
         if (zvar == ZPROD_TMA) {
             SPM_TRY((launch_ztma<R, L>(W2, spec, tw, nb, err, s)));
+            done = true;
+        }
+    }
+    if constexpr (L == 128 || L == 256 || L == 512) {
+        if (zvar == ZPROD_E16) {
+            constexpr size_t sm16 = zp16<R, L>::smem();
+            static bool a16 = false;
+            if (!a16) {
+                allow_smem(k3_zpass<R, L>, sm16);
+                a16 = true;
+            }
+            launch_pdl(k3_zpass<R, L>, dim3((unsigned)(L2 / zp16<R, L>::TX), nb), dim3(zp16<R, L>::THREADS), sm16, s,
+                       W2, spec, tw);
+            done = true;
+        }
+    }
+    if constexpr (L >= 32) {
+        if (!done && zvar == ZPROD_STAGED) {
+            constexpr size_t smz = zst<R, L>::smem;
+            static bool ast = false;
+            if (!ast) {
+                allow_smem(k2_zstaged<R, L>, smz);
+                ast = true;
+            }
+            launch_pdl(k2_zstaged<R, L>, dim3((unsigned)(L2 / TX), nb), dim3(zst<R, L>::THREADS), smz, s, W2, spec, tw);
             done = true;
         }
     }
@@ -696,6 +1082,11 @@ spm_status apply_chunk_v2(const typename cplx_of<R>::type *xb, typename cplx_of<
         }
     }
     if (!done) launch_pdl(k2_zprod1<R, L>, dim3((unsigned)(L2 / TX), nb), dim3(THR), sm_zprod, s, W2, spec, tw);
+    if (fused_done) {
+        if constexpr (L == 64 || L == 128)
+            launch_pdl(k2_yxinv<R, L>, dim3(n, 3, nb), dim3(256), xyf<R, L>::smem, s, (const C *)W2, xb, yb, tw);
+        return SPM_OK;
+    }
     if constexpr (line_elems(L) == 8 && n % 2 == 0)
         launch_pdl(k2_cols2<R, L, 1, false>, dim3(L / TX, n / 2, nb * 3), dim3(THR), 2 * sm_cols, s, (const C *)W2, W1,
                    n, (long)L, 3, 4 * (long)n * L2, (long)n * L2, L2, 3 * n2 * L, n2 * L, n * (long)L, tw);
@@ -740,6 +1131,10 @@ spm_status run_chunk(int L, const typename cplx_of<R>::type *xb, typename cplx_o
 // later apply; during stream capture the default kernel is used untimed.
 std::atomic<int> g_zplan[2][10];
 std::atomic<int> g_zplan_init(0);
+// per-apply ms of each candidate when the plan timed them (0: not timed)
+float g_ztime[2][10][5];
+float g_ztime_fused[2][10]; // the chosen z-pass with fused x and y passes (0: not timed)
+std::mutex g_ztime_mu;
 
 int len_index(int L)
 {
@@ -772,10 +1167,12 @@ spm_status choose_zplan(int L, const typename cplx_of<R>::type *xb, typename cpl
     int z = zplan_get(pi, L);
     if (z >= 0) { *zvar = z; return SPM_OK; }
     const int fallback = line_elems(L) == 8 ? ZPROD_FOUR : ZPROD_ONE;
-    int cands[3], nc = 0;
+    int cands[5], nc = 0;
     if (line_elems(L) == 8) cands[nc++] = ZPROD_FOUR;
     if (line_elems(L) != 8 || L >= 32) cands[nc++] = ZPROD_ONE;
     if (L >= 32) cands[nc++] = ZPROD_TMA;
+    if (L == 128 || L == 256 || L == 512) cands[nc++] = ZPROD_E16;
+    if (L >= 32) cands[nc++] = ZPROD_STAGED;
     if (nc == 1) { g_zplan[pi][len_index(L)].store(cands[0]); *zvar = cands[0]; return SPM_OK; }
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     SPM_CUDA_TRY(cudaStreamIsCapturing(s, &cap));
@@ -786,17 +1183,44 @@ spm_status choose_zplan(int L, const typename cplx_of<R>::type *xb, typename cpl
     float best = 0;
     int best_z = fallback;
     spm_status st = SPM_OK;
+    const int reps = L >= 512 ? 3 : (L >= 256 ? 5 : 10);
+    float times[5] = {0, 0, 0, 0, 0};
     for (int ci = 0; ci < nc; ++ci) {
         const int cand = cands[ci];
         st = run_chunk<R>(L, xb, yb, m, p, spec, tw, W1, W2, nb, cand, err, s); // warm-up
         if (st != SPM_OK) break;
         cudaEventRecord(e0, s);
-        for (int r = 0; r < 3 && st == SPM_OK; ++r) st = run_chunk<R>(L, xb, yb, m, p, spec, tw, W1, W2, nb, cand, err, s);
+        for (int r = 0; r < reps && st == SPM_OK; ++r) st = run_chunk<R>(L, xb, yb, m, p, spec, tw, W1, W2, nb, cand, err, s);
         cudaEventRecord(e1, s);
         if (st != SPM_OK || cudaEventSynchronize(e1) != cudaSuccess) { st = st != SPM_OK ? st : SPM_ERR_CUDA; break; }
         float ms = 0;
         cudaEventElapsedTime(&ms, e0, e1);
+        times[cand] = ms / reps;
         if (ci == 0 || ms < best) { best = ms; best_z = cand; }
+    }
+    float fused_ms = 0;
+    if (st == SPM_OK && (L == 64 || L == 128)) {
+        // the best z-pass again with the x and y passes fused per plane
+        const int cand = best_z | ZPLAN_FUSED_XY;
+        st = run_chunk<R>(L, xb, yb, m, p, spec, tw, W1, W2, nb, cand, err, s);
+        if (st == SPM_OK) {
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < reps && st == SPM_OK; ++r) st = run_chunk<R>(L, xb, yb, m, p, spec, tw, W1, W2, nb, cand, err, s);
+            cudaEventRecord(e1, s);
+            if (st == SPM_OK && cudaEventSynchronize(e1) == cudaSuccess) {
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                fused_ms = ms / reps;
+                if (ms < best) { best = ms; best_z = cand; }
+            } else if (st == SPM_OK) {
+                st = SPM_ERR_CUDA;
+            }
+        }
+    }
+    if (st == SPM_OK) {
+        std::lock_guard<std::mutex> lock(g_ztime_mu);
+        for (int v = 0; v < 5; ++v) g_ztime[pi][len_index(L)][v] = times[v];
+        g_ztime_fused[pi][len_index(L)] = fused_ms;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -840,7 +1264,7 @@ spm_status apply_A_typed(spm_problem_s *P, const void *xv, void *yv, int nrhs, c
 // Q gather in one launch of 256-thread blocks of three kinds (block-uniform
 // branch), boundary blocks first so that their latency overlaps the interior:
 // * face blocks: the points with exactly one coordinate on the boundary belong
-//   to one of six face classes; a block owns a 32 x 8 tile of one face, stages
+//   to one of six face classes; a block owns a 32 x 4 tile of one face, stages
 //   the face layer and the next layer inward (three components, one-point halo)
 //   and its class's 18-neighbour coefficients (remapped to face-local order) in
 //   shared memory, and each thread forms its point's three outputs;
@@ -849,17 +1273,17 @@ spm_status apply_A_typed(spm_problem_s *P, const void *xv, void *yv, int nrhs, c
 //   (of 81) from the expanded table [cls][d][o][c] (zero outside the class
 //   neighbourhood, which is also where a neighbour would leave the grid) and
 //   the warp sums its partials;
-// * interior blocks (1 <= i_d <= n-2, one class): a 32 x 8 x QZ tile whose three
+// * interior blocks (1 <= i_d <= n-2, one class): a 32 x 4 x QZ tile whose three
 //   components plus a one-point halo are staged in shared memory; each thread
 //   owns QZ = 4 points stacked along z, so every staged value it loads feeds the
 //   three z-offsets of up to three of its points (6 loads per (d, o1, o2) serve
 //   36 complex MACs per output component instead of one load per MAC); the
 //   class's 243 coefficients arrive as a by-value kernel parameter, so they sit
 //   in the constant bank, and each feeds QZ points once in registers.
-constexpr int Q_THREADS = 256;
-constexpr int QX = 32, QY = 8, QZ = 4;
+constexpr int Q_THREADS = 128;
+constexpr int QX = 32, QY = 4, QZ = 4;
 constexpr int QHX = QX + 2, QHY = QY + 2, QHZ = QZ + 2, QH = QHX * QHY * QHZ;
-constexpr int QF_U = 32, QF_W = 8;
+constexpr int QF_U = 32, QF_W = 4;
 constexpr int QF_HU = QF_U + 2, QF_HW = QF_W + 2, QF_HALO = 3 * 2 * QF_HW * QF_HU;
 constexpr int Q_SMEM = (3 * QH > QF_HALO + 162) ? 3 * QH : QF_HALO + 162; // complex elements
 static_assert(QX * QY == Q_THREADS && QF_U * QF_W == Q_THREADS, "Q block shapes");
@@ -901,15 +1325,18 @@ __device__ __forceinline__ void q_interior_block(int blk, const C *__restrict__ 
     const int tiles_x = (m + QX - 1) / QX, tiles_y = (m + QY - 1) / QY;
     const int txy = blk % (tiles_x * tiles_y), tz = blk / (tiles_x * tiles_y);
     const int tx0 = 1 + (txy % tiles_x) * QX, ty0 = 1 + (txy / tiles_x) * QY, tz0 = 1 + tz * QZ;
-    // halo [d][hz][hy][hx], x fastest: each warp's loads below read 32 consecutive x
+    // halo [d][hz][hy][hx], x fastest: each warp's loads below read 32 consecutive x.
+    // All copies are issued before any is waited for (cp.async, zero fill outside
+    // the grid), so their latencies overlap.
     for (int i = threadIdx.x; i < 3 * QH; i += Q_THREADS) {
         int d = i / QH, h = i % QH;
         int hx = h % QHX, hy = (h / QHX) % QHY, hz = h / (QHX * QHY);
         int gx = tx0 + hx - 1, gy = ty0 + hy - 1, gz = tz0 + hz - 1;
-        C val = czero<C>();
-        if (gx < n && gy < n && gz < n) val = vb[d * n3 + ((long)gz * n + gy) * n + gx];
-        sv[i] = val;
+        const bool in = gx < n && gy < n && gz < n;
+        cp_async_zfill<sizeof(C)>(&sv[i], in ? vb + d * n3 + ((long)gz * n + gy) * n + gx : vb, in);
     }
+    cp_async_commit();
+    cp_async_wait<0>();
     __syncthreads();
     const int lx = threadIdx.x % QX, ly = threadIdx.x / QX;
     const int i1 = tx0 + lx, i2 = ty0 + ly;
@@ -1000,10 +1427,11 @@ __device__ __forceinline__ void q_face_block(int blk, const C *__restrict__ vb, 
     for (int i = threadIdx.x; i < QF_HALO; i += Q_THREADS) {
         const int hu = i % QF_HU, hw = (i / QF_HU) % QF_HW, la = (i / (QF_HU * QF_HW)) % 2, d = i / (2 * QF_HU * QF_HW);
         const int gu = u0 + hu, gw = w0 + hw; // halo starts one point before the first face point (u = 1)
-        C val = czero<C>();
-        if (gu < n && gw < n) val = vb[d * n3 + (ia0 + (la ? inward : 0)) * sa_ + gu * su + gw * sw];
-        sv[i] = val;
+        const bool in = gu < n && gw < n;
+        cp_async_zfill<sizeof(C)>(&sv[i], in ? vb + d * n3 + (ia0 + (la ? inward : 0)) * sa_ + gu * su + gw * sw : vb, in);
     }
+    cp_async_commit();
+    cp_async_wait<0>();
     __syncthreads();
     const int lu = threadIdx.x % QF_U, lw = threadIdx.x / QF_U;
     const int pu = 1 + u0 + lu, pw = 1 + w0 + lw;
@@ -1168,7 +1596,8 @@ spm_status spm_build_qtable(spm_problem_s *P)
 static int zplan_supported(int L)
 {
     const bool e8 = !(L == 96 || L == 192);
-    return (e8 ? 1 << ZPROD_FOUR : 0) | ((!e8 || L >= 32) ? 1 << ZPROD_ONE : 0) | (L >= 32 ? 1 << ZPROD_TMA : 0);
+    return (e8 ? 1 << ZPROD_FOUR : 0) | ((!e8 || L >= 32) ? 1 << ZPROD_ONE : 0) | (L >= 32 ? 1 << ZPROD_TMA : 0) |
+           ((L == 128 || L == 256 || L == 512) ? 1 << ZPROD_E16 : 0) | (L >= 32 ? 1 << ZPROD_STAGED : 0);
 }
 
 spm_status spm_wait_selftest_impl(spm_problem_s *P)
@@ -1183,7 +1612,10 @@ spm_status spm_apply_plan_impl(int prec, int L, int *get, const int *set)
     if (len_index(L) > 8) { spm_set_error("no apply plan for FFT length %d", L); return SPM_ERR_INVALID_ARG; }
     const int pi = prec == SPM_C128 ? 0 : 1;
     if (set) {
-        if (*set != -1 && (*set < 0 || *set > 2 || !(zplan_supported(L) & (1 << *set)))) {
+        const int zpart = *set & (ZPLAN_FUSED_XY - 1);
+        const bool fz = *set >= 0 && (*set & ZPLAN_FUSED_XY) != 0;
+        if (*set != -1 && (*set < 0 || *set > (ZPLAN_FUSED_XY | 4) || !(zplan_supported(L) & (1 << zpart)) ||
+                           (fz && L != 64 && L != 128))) {
             spm_set_error("z-pass variant %d is not available for FFT length %d", *set, L);
             return SPM_ERR_INVALID_ARG;
         }
@@ -1191,6 +1623,104 @@ spm_status spm_apply_plan_impl(int prec, int L, int *get, const int *set)
         g_zplan[pi][len_index(L)].store(*set);
     }
     if (get) *get = zplan_get(pi, L);
+    return SPM_OK;
+}
+
+// ---- persistence of the apply plans (JSON) ----
+static const int k_plan_lengths[9] = {8, 16, 32, 64, 128, 256, 512, 96, 192};
+
+static std::string device_name()
+{
+    int dev = 0;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return "unknown";
+    return prop.name;
+}
+
+spm_status spm_save_plans_impl(const char *path)
+{
+    std::string out = "{\n  \"device\": \"" + device_name() + "\",\n  \"plans\": [";
+    bool first = true;
+    for (int pi = 0; pi < 2; ++pi)
+        for (int li = 0; li < 9; ++li) {
+            const int L = k_plan_lengths[li];
+            const int z = zplan_get(pi, L);
+            if (z < 0) continue;
+            char buf[256];
+            float t[5];
+            {
+                std::lock_guard<std::mutex> lock(g_ztime_mu);
+                for (int v = 0; v < 5; ++v) t[v] = g_ztime[pi][li][v];
+            }
+            float tf;
+            {
+                std::lock_guard<std::mutex> lock(g_ztime_mu);
+                tf = g_ztime_fused[pi][li];
+            }
+            snprintf(buf, sizeof buf,
+                     "%s\n    {\"prec\": \"%s\", \"L\": %d, \"variant\": %d, \"ms\": [%.6g, %.6g, %.6g, %.6g, %.6g], "
+                     "\"fused_xy_ms\": %.6g}",
+                     first ? "" : ",", pi == 0 ? "c128" : "c64", L, z, t[0], t[1], t[2], t[3], t[4], tf);
+            out += buf;
+            first = false;
+        }
+    out += "\n  ]\n}\n";
+    FILE *f = fopen(path, "w");
+    if (!f) { spm_set_error("cannot open %s for writing", path); return SPM_ERR_INVALID_ARG; }
+    const size_t w = fwrite(out.data(), 1, out.size(), f);
+    fclose(f);
+    if (w != out.size()) { spm_set_error("short write to %s", path); return SPM_ERR_INVALID_ARG; }
+    return SPM_OK;
+}
+
+// Reads the file written above: the device name must match the current
+// device's; each {"prec", "L", "variant"} entry with a variant the length
+// supports is installed.  *loaded = number of entries installed.
+spm_status spm_load_plans_impl(const char *path, int *loaded)
+{
+    FILE *f = fopen(path, "r");
+    if (!f) { spm_set_error("cannot open %s", path); return SPM_ERR_INVALID_ARG; }
+    std::string txt;
+    char buf[4096];
+    size_t r;
+    while ((r = fread(buf, 1, sizeof buf, f)) > 0) txt.append(buf, r);
+    fclose(f);
+    auto str_after = [&](size_t pos, const char *key, std::string &val) -> bool {
+        size_t k = txt.find(key, pos);
+        if (k == std::string::npos) return false;
+        size_t q0 = txt.find('"', txt.find(':', k) + 1);
+        size_t q1 = q0 == std::string::npos ? q0 : txt.find('"', q0 + 1);
+        if (q1 == std::string::npos) return false;
+        val = txt.substr(q0 + 1, q1 - q0 - 1);
+        return true;
+    };
+    std::string dev;
+    if (!str_after(0, "\"device\"", dev)) { spm_set_error("%s: no device name", path); return SPM_ERR_INVALID_ARG; }
+    if (dev != device_name()) {
+        spm_set_error("%s was tuned on \"%s\", this device is \"%s\"", path, dev.c_str(), device_name().c_str());
+        return SPM_ERR_INVALID_ARG;
+    }
+    int count = 0;
+    size_t pos = txt.find("\"plans\"");
+    while (pos != std::string::npos) {
+        size_t ob = txt.find('{', pos);
+        if (ob == std::string::npos) break;
+        size_t cb = txt.find('}', ob);
+        if (cb == std::string::npos) break;
+        const std::string obj = txt.substr(ob, cb - ob + 1);
+        pos = cb + 1;
+        int L = 0, z = -1;
+        char pr[8] = "";
+        const size_t kp = obj.find("\"prec\""), kl = obj.find("\"L\""), kv = obj.find("\"variant\"");
+        if (kp == std::string::npos || kl == std::string::npos || kv == std::string::npos) continue;
+        if (sscanf(obj.c_str() + obj.find(':', kp) + 1, " \"%7[^\"]\"", pr) != 1) continue;
+        if (sscanf(obj.c_str() + obj.find(':', kl) + 1, " %d", &L) != 1) continue;
+        if (sscanf(obj.c_str() + obj.find(':', kv) + 1, " %d", &z) != 1) continue;
+        const int prec = strcmp(pr, "c128") == 0 ? SPM_C128 : (strcmp(pr, "c64") == 0 ? SPM_C64 : -1);
+        if (prec < 0 || len_index(L) > 8) continue;
+        if (spm_apply_plan_impl(prec, L, nullptr, &z) == SPM_OK) ++count;
+    }
+    if (loaded) *loaded = count;
     return SPM_OK;
 }
 

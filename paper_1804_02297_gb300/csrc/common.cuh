@@ -115,6 +115,7 @@ struct DevBuf {
 
 // ------------------------------------------------------------ sparse factor
 struct NDFactor; // nested-dissection multifrontal factor (sparse.cu)
+struct CufftState; // plans and padded arrays of the cuFFT comparison apply (cufft_apply.cu)
 
 // ------------------------------------------------------------ the handle
 struct spm_problem_s {
@@ -153,6 +154,8 @@ struct spm_problem_s {
     };
     FactorInfo fac_info[2]; // [0] complex128 factor, [1] complex64 factor
 
+    CufftState *cufft = nullptr; // comparison apply through cuFFT (created on first use)
+
     // solver workspace
     DevBuf kry;      // A x inside apply_QA
     DevBuf gmres_ws; // GMRES vectors and reductions of spm_solve
@@ -162,6 +165,8 @@ struct spm_problem_s {
 spm_status spm_apply_A_impl(spm_problem_s *P, int prec, const void *x, void *y, int nrhs, cudaStream_t s);
 spm_status spm_apply_Q_impl(spm_problem_s *P, int prec, const void *v, void *y, int nrhs, cudaStream_t s);
 spm_status spm_apply_plan_impl(int prec, int L, int *get, const int *set);
+spm_status spm_save_plans_impl(const char *path);
+spm_status spm_load_plans_impl(const char *path, int *loaded);
 spm_status spm_wait_selftest_impl(spm_problem_s *P);
 spm_status spm_build_qtable(spm_problem_s *P);
 spm_status spm_build_spectra(spm_problem_s *P);
@@ -172,7 +177,16 @@ spm_status spm_factor_impl(spm_problem_s *P, int prec);
 spm_status spm_factor_tree_impl(spm_problem_s *P, int prec, int variant);
 spm_status spm_solveS_impl(spm_problem_s *P, int prec, const void *b, void *x, int nrhs, cudaStream_t s);
 void spm_factor_free(NDFactor *f);
-int spm_factor_gemm_mode();
-void spm_set_factor_gemm_mode(int m);
+void spm_cufft_free(CufftState *c);
+// dense front kernels (dense.cu)
+struct DenseWork;
+DenseWork *spm_dense_work_new();
+void spm_dense_work_free(DenseWork *w);
+template <typename C>
+spm_status spm_dense_gemm(int m, int n, int k, double alpha, const C *A, long lda, const C *B, long ldb, double beta,
+                          C *Cm, long ldc, cudaStream_t s);
+template <typename C>
+spm_status spm_dense_inverse(int m, C *A, long lda, C *out, long ldo, double tau, int *raised_dev, int *err_dev,
+                             DenseWork *W, cudaStream_t s);
 spm_status spm_solve_impl(spm_problem_s *P, int prec, const void *g, void *x, int nrhs, double tol,
                           int maxit, int restart, spm_solve_info *info);

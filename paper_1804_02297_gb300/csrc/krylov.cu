@@ -221,114 +221,150 @@ spm_status axpy_multi(const C *V, long vstride, int nvec, const double2 *h, int 
     return SPM_OK;
 }
 
+// ---- the small FP64 problem of GMRES on the device, one thread per RHS ----
+// Per right-hand side b the cycle keeps, in device memory: the Hessenberg
+// matrix H[b] ((restart + 1) x restart, row i column j at i * restart + j), the
+// Givens rotations cs[b][i], sn[b][i], the rotated residual vector g[b][i], beta
+// = ||v_0||, and whether b is still active.
+struct GmresSmall {
+    double2 *H, *cs, *sn, *g;
+    double *beta, *rtol, *scale;
+    int *active, *count; // count[0]: RHS still active; count[1]: non-finite values seen
+};
+
+// after v_0 = S^-1 Q r: beta = ||v_0|| (nn[b*ld] holds <v_0, v_0>), g = beta e_1
+__global__ void k_cycle_init(GmresSmall gs, const double2 *__restrict__ nn, int ld, int restart, int nrhs)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nrhs) return;
+    const double beta = sqrt(fmax(nn[(long)b * ld].x, 0.0));
+    const bool ok = beta > 0 && isfinite(beta);
+    gs.beta[b] = beta;
+    gs.active[b] = ok ? 1 : 0;
+    gs.scale[b] = ok ? 1.0 / beta : 0.0;
+    for (int i = 0; i <= restart; ++i) gs.g[(long)b * (restart + 1) + i] = make_double2(i == 0 ? beta : 0.0, 0.0);
+    for (long i = 0; i < (long)(restart + 1) * restart; ++i) gs.H[(long)b * (restart + 1) * restart + i] = make_double2(0, 0);
+    if (ok) atomicAdd(&gs.count[0], 1);
+}
+
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ double2 zconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 zadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+
+// Arnoldi step j: column j of H from the two Gram-Schmidt passes (h1, h2) and
+// ||w|| (nn), the previous rotations applied, a new rotation that zeroes
+// H[j+1][j], g rotated; scale = 1/||w|| for normalising v_{j+1}; a RHS whose
+// |g[j+1]| <= rtol beta (or whose ||w|| vanished) becomes inactive.
+__global__ void k_arnoldi_givens(GmresSmall gs, const double2 *__restrict__ h1, const double2 *__restrict__ h2,
+                                 const double2 *__restrict__ nn, int ld, int j, int restart, int nrhs)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nrhs) return;
+    if (!gs.active[b]) { gs.scale[b] = 0.0; return; }
+    double2 *H = gs.H + (long)b * (restart + 1) * restart;
+    double2 *cs = gs.cs + (long)b * restart, *sn = gs.sn + (long)b * restart, *g = gs.g + (long)b * (restart + 1);
+    for (int i = 0; i <= j; ++i) H[i * restart + j] = zadd(h1[(long)b * ld + i], h2[(long)b * ld + i]);
+    const double hn = sqrt(fmax(nn[(long)b * ld].x, 0.0));
+    if (!isfinite(hn)) { atomicAdd(&gs.count[1], 1); gs.active[b] = 0; gs.scale[b] = 0.0; return; }
+    H[(j + 1) * restart + j] = make_double2(hn, 0.0);
+    gs.scale[b] = hn > 1e-300 ? 1.0 / hn : 0.0;
+    for (int i = 0; i < j; ++i) {
+        const double2 a = H[i * restart + j], c = H[(i + 1) * restart + j];
+        H[i * restart + j] = zadd(zmul(zconj(cs[i]), a), zmul(zconj(sn[i]), c));
+        const double2 ms = make_double2(-sn[i].x, -sn[i].y);
+        H[(i + 1) * restart + j] = zadd(zmul(ms, a), zmul(cs[i], c));
+    }
+    const double2 a = H[j * restart + j], c = H[(j + 1) * restart + j];
+    const double den = sqrt(a.x * a.x + a.y * a.y + c.x * c.x + c.y * c.y);
+    if (den == 0.0) { cs[j] = make_double2(1.0, 0.0); sn[j] = make_double2(0.0, 0.0); }
+    else { cs[j] = make_double2(a.x / den, a.y / den); sn[j] = make_double2(c.x / den, c.y / den); }
+    H[j * restart + j] = make_double2(den, 0.0);
+    H[(j + 1) * restart + j] = make_double2(0.0, 0.0);
+    const double2 gj = g[j];
+    const double2 ms = make_double2(-sn[j].x, -sn[j].y);
+    g[j + 1] = zmul(ms, gj);
+    g[j] = zmul(zconj(cs[j]), gj);
+    const double r = sqrt(g[j + 1].x * g[j + 1].x + g[j + 1].y * g[j + 1].y);
+    if (r <= gs.rtol[b] * gs.beta[b] || hn <= 1e-300) gs.active[b] = 0;
+    else atomicAdd(&gs.count[0], 1);
+}
+
+// back substitution H y = g over the leading m columns (fewer where a RHS
+// stopped early: its trailing diagonal entries are zero); y -> coef[b*ld + i]
+__global__ void k_backsolve(GmresSmall gs, double2 *coef, int ld, int m, int restart, int nrhs)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nrhs) return;
+    const double2 *H = gs.H + (long)b * (restart + 1) * restart, *g = gs.g + (long)b * (restart + 1);
+    double2 *y = coef + (long)b * ld;
+    int mb = m;
+    while (mb > 0 && H[(mb - 1) * restart + (mb - 1)].x == 0.0 && H[(mb - 1) * restart + (mb - 1)].y == 0.0) --mb;
+    for (int i = 0; i < ld; ++i) y[i] = make_double2(0, 0);
+    for (int i = mb - 1; i >= 0; --i) {
+        double2 acc = g[i];
+        for (int q = i + 1; q < mb; ++q) {
+            const double2 t = zmul(H[i * restart + q], y[q]);
+            acc.x -= t.x;
+            acc.y -= t.y;
+        }
+        const double2 d = H[i * restart + i];
+        const double dd = d.x * d.x + d.y * d.y;
+        y[i] = make_double2((acc.x * d.x + acc.y * d.y) / dd, (acc.y * d.x - acc.x * d.y) / dd);
+    }
+}
+
 // One preconditioned GMRES(restart) cycle for all right-hand sides, zero initial
 // guess: d = argmin over the Krylov space of ||S^{-1} Q (r - A d)||.  Stops
 // early when every active RHS reaches relative preconditioned residual rtol[b].
 template <typename R>
 spm_status gmres_cycle(spm_problem_s *P, int prec, const typename cplx_of<R>::type *r, typename cplx_of<R>::type *d,
-                       int nrhs, int restart, const std::vector<double> &rtol, typename cplx_of<R>::type *V,
-                       typename cplx_of<R>::type *tmp, double2 *partial, double2 *hdev, double *sdev, int *iters,
-                       cudaStream_t s)
+                       int nrhs, int restart, typename cplx_of<R>::type *V, typename cplx_of<R>::type *tmp,
+                       double2 *partial, double2 *h1, double2 *h2, double2 *nn, const GmresSmall &gs, int *count_host,
+                       int *iters, cudaStream_t s)
 {
     using C = typename cplx_of<R>::type;
-    typedef std::complex<double> cd;
     const long N = 3L * P->n * P->n * P->n;
     const long vstride = N * nrhs;
     const int ld = restart + 2;
-    std::vector<double2> hh((size_t)nrhs * ld);
-    std::vector<double> beta(nrhs), scl(nrhs);
-    std::vector<std::vector<cd>> H(nrhs, std::vector<cd>((size_t)(restart + 1) * restart));
-    std::vector<std::vector<cd>> cs(nrhs, std::vector<cd>(restart)), sn(nrhs, std::vector<cd>(restart));
-    std::vector<std::vector<cd>> gv(nrhs, std::vector<cd>(restart + 1));
-    std::vector<char> active(nrhs, 1);
-    C *w = V + (long)(restart)*vstride; // reuse slot for w until V_{j+1} is formed
+    const unsigned sb = (unsigned)((nrhs + 63) / 64);
+    C *w = V + (long)(restart)*vstride;
 
     // v0 = S^{-1} Q r / beta
     SPM_TRY(spm_apply_Q_impl(P, prec, r, tmp, nrhs, s));
     SPM_TRY(spm_solveS_impl(P, prec, tmp, V, nrhs, s));
-    SPM_TRY(dots<C>(V, vstride, 1, V, N, nrhs, partial, hdev, ld, s));
-    SPM_CUDA_TRY(cudaMemcpyAsync(hh.data(), hdev, sizeof(double2) * nrhs * ld, cudaMemcpyDeviceToHost, s));
+    SPM_TRY(dots<C>(V, vstride, 1, V, N, nrhs, partial, nn, ld, s));
+    SPM_CUDA_TRY(cudaMemsetAsync(gs.count, 0, 2 * sizeof(int), s));
+    k_cycle_init<<<sb, 64, 0, s>>>(gs, nn, ld, restart, nrhs);
+    k_scale_copy<C, C><<<nblocks(vstride), 256, 0, s>>>(V, V, gs.scale, N, nrhs);
+    SPM_CUDA_TRY(cudaMemcpyAsync(count_host, gs.count, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
     SPM_CUDA_TRY(cudaStreamSynchronize(s));
-    for (int b = 0; b < nrhs; ++b) {
-        beta[b] = sqrt(fmax(hh[(size_t)b * ld].x, 0.0));
-        if (!(beta[b] > 0) || !isfinite(beta[b])) active[b] = 0;
-        scl[b] = beta[b] > 0 ? 1.0 / beta[b] : 0.0;
-        gv[b][0] = beta[b];
-    }
-    SPM_CUDA_TRY(cudaMemcpyAsync(sdev, scl.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
-    k_scale_copy<C, C><<<nblocks(vstride), 256, 0, s>>>(V, V, sdev, N, nrhs);
     int j = 0;
-    for (; j < restart; ++j) {
-        bool any = false;
-        for (int b = 0; b < nrhs; ++b) any |= active[b] != 0;
-        if (!any) break;
+    for (; j < restart && count_host[0] > 0; ++j) {
         C *vj = V + (long)j * vstride;
         w = V + (long)(j + 1) * vstride;
         SPM_TRY(spm_apply_A_impl(P, prec, vj, w, nrhs, s));        // w = A v_j
         SPM_TRY(spm_apply_Q_impl(P, prec, w, tmp, nrhs, s));       // tmp = Q A v_j
         SPM_TRY(spm_solveS_impl(P, prec, tmp, w, nrhs, s));        // w = S^{-1} Q A v_j
-        // classical Gram-Schmidt twice
-        SPM_TRY(dots<C>(V, vstride, j + 1, w, N, nrhs, partial, hdev, ld, s));
-        SPM_TRY(axpy_multi<C>(V, vstride, j + 1, hdev, ld, w, N, nrhs, -1.0, s));
-        SPM_CUDA_TRY(cudaMemcpyAsync(hh.data(), hdev, sizeof(double2) * nrhs * ld, cudaMemcpyDeviceToHost, s));
-        SPM_TRY(dots<C>(V, vstride, j + 1, w, N, nrhs, partial, hdev, ld, s));
-        SPM_TRY(axpy_multi<C>(V, vstride, j + 1, hdev, ld, w, N, nrhs, -1.0, s));
-        std::vector<double2> h2((size_t)nrhs * ld);
-        SPM_CUDA_TRY(cudaMemcpyAsync(h2.data(), hdev, sizeof(double2) * nrhs * ld, cudaMemcpyDeviceToHost, s));
-        // ||w|| after orthogonalisation: dot of w with itself (w sits at slot j+1)
-        SPM_TRY(dots<C>(w, vstride, 1, w, N, nrhs, partial, hdev, ld, s));
-        std::vector<double2> nn((size_t)nrhs * ld);
-        SPM_CUDA_TRY(cudaMemcpyAsync(nn.data(), hdev, sizeof(double2) * nrhs * ld, cudaMemcpyDeviceToHost, s));
-        SPM_CUDA_TRY(cudaStreamSynchronize(s));
+        // classical Gram-Schmidt twice, FP64 coefficients
+        SPM_TRY(dots<C>(V, vstride, j + 1, w, N, nrhs, partial, h1, ld, s));
+        SPM_TRY(axpy_multi<C>(V, vstride, j + 1, h1, ld, w, N, nrhs, -1.0, s));
+        SPM_TRY(dots<C>(V, vstride, j + 1, w, N, nrhs, partial, h2, ld, s));
+        SPM_TRY(axpy_multi<C>(V, vstride, j + 1, h2, ld, w, N, nrhs, -1.0, s));
+        SPM_TRY(dots<C>(w, vstride, 1, w, N, nrhs, partial, nn, ld, s)); // ||w||^2 (w sits at slot j+1)
+        SPM_CUDA_TRY(cudaMemsetAsync(gs.count, 0, sizeof(int), s));
+        k_arnoldi_givens<<<sb, 64, 0, s>>>(gs, h1, h2, nn, ld, j, restart, nrhs);
+        k_scale_copy<C, C><<<nblocks(vstride), 256, 0, s>>>(w, w, gs.scale, N, nrhs);
+        SPM_CUDA_TRY(cudaMemcpyAsync(count_host, gs.count, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        SPM_CUDA_TRY(cudaStreamSynchronize(s)); // the only host round trip of an iteration: a convergence count
         ++*iters;
-        for (int b = 0; b < nrhs; ++b) {
-            std::vector<cd> &Hb = H[b];
-            for (int i = 0; i <= j; ++i) {
-                double2 a = hh[(size_t)b * ld + i], c2 = h2[(size_t)b * ld + i];
-                Hb[(size_t)i * restart + j] = active[b] ? cd(a.x + c2.x, a.y + c2.y) : cd(0, 0);
-            }
-            double hn = sqrt(fmax(nn[(size_t)b * ld].x, 0.0));
-            if (!isfinite(hn)) { spm_set_error("NaN in GMRES"); return SPM_ERR_NUMERICAL; }
-            Hb[(size_t)(j + 1) * restart + j] = active[b] ? hn : 0.0;
-            scl[b] = (active[b] && hn > 1e-300) ? 1.0 / hn : 0.0;
-            if (!active[b]) continue;
-            for (int i = 0; i < j; ++i) {
-                cd a = Hb[(size_t)i * restart + j], bb = Hb[(size_t)(i + 1) * restart + j];
-                Hb[(size_t)i * restart + j] = std::conj(cs[b][i]) * a + std::conj(sn[b][i]) * bb;
-                Hb[(size_t)(i + 1) * restart + j] = -sn[b][i] * a + cs[b][i] * bb;
-            }
-            cd a = Hb[(size_t)j * restart + j], bb = Hb[(size_t)(j + 1) * restart + j];
-            double den = sqrt(std::norm(a) + std::norm(bb));
-            if (den == 0.0) { cs[b][j] = 1.0; sn[b][j] = 0.0; }
-            else { cs[b][j] = a / den; sn[b][j] = bb / den; }
-            Hb[(size_t)j * restart + j] = den;
-            Hb[(size_t)(j + 1) * restart + j] = 0.0;
-            gv[b][j + 1] = -sn[b][j] * gv[b][j];
-            gv[b][j] = std::conj(cs[b][j]) * gv[b][j];
-            if (std::abs(gv[b][j + 1]) <= rtol[b] * beta[b] || hn <= 1e-300) active[b] = 0;
-        }
-        SPM_CUDA_TRY(cudaMemcpyAsync(sdev, scl.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
-        k_scale_copy<C, C><<<nblocks(vstride), 256, 0, s>>>(w, w, sdev, N, nrhs);
+        if (count_host[1]) { spm_set_error("NaN in GMRES"); return SPM_ERR_NUMERICAL; }
     }
-    // d = sum_i y_i v_i with H y = g (upper triangular, per RHS)
+    // d = sum_i y_i v_i with H y = g (upper triangular, per RHS, on the device)
     const int m = j;
-    std::vector<double2> ycoef((size_t)nrhs * ld, make_double2(0, 0));
-    for (int b = 0; b < nrhs; ++b) {
-        int mb = m;
-        // columns beyond the RHS's convergence point are zero rows/cols: solve the leading block
-        while (mb > 0 && std::abs(H[b][(size_t)(mb - 1) * restart + (mb - 1)]) == 0.0) --mb;
-        std::vector<cd> y(mb);
-        for (int i = mb - 1; i >= 0; --i) {
-            cd acc = gv[b][i];
-            for (int q = i + 1; q < mb; ++q) acc -= H[b][(size_t)i * restart + q] * y[q];
-            y[i] = acc / H[b][(size_t)i * restart + i];
-        }
-        for (int i = 0; i < mb; ++i) ycoef[(size_t)b * ld + i] = make_double2(y[i].real(), y[i].imag());
-    }
-    SPM_CUDA_TRY(cudaMemcpyAsync(hdev, ycoef.data(), sizeof(double2) * nrhs * ld, cudaMemcpyHostToDevice, s));
+    k_backsolve<<<sb, 64, 0, s>>>(gs, h1, ld, m, restart, nrhs);
     SPM_CUDA_TRY(cudaMemsetAsync(d, 0, sizeof(C) * vstride, s));
-    SPM_TRY(axpy_multi<C>(V, vstride, m, hdev, ld, d, N, nrhs, 1.0, s));
-    SPM_CUDA_TRY(cudaStreamSynchronize(s));
+    SPM_TRY(axpy_multi<C>(V, vstride, m, h1, ld, d, N, nrhs, 1.0, s));
+    SPM_CUDA_TRY(cudaGetLastError());
     return SPM_OK;
 }
 
@@ -356,9 +392,10 @@ spm_status solve_typed(spm_problem_s *P, int mode, const double2 *g, double2 *x,
     const long vstride = N * nrhs;
     const int ld = restart + 2;
     // workspace: r (c128), Ax (c128), V (restart+1), d, tmp (inner precision), reductions
+    const size_t small = sizeof(double2) * (size_t)nrhs * (3 * ld + (restart + 1) * restart + 2 * restart + restart + 1) +
+                         sizeof(double) * 3 * (size_t)nrhs + sizeof(int) * ((size_t)nrhs + 2);
     size_t bytes = sizeof(double2) * 2 * vstride + sizeof(C) * (size_t)(restart + 3) * vstride +
-                   sizeof(double2) * (size_t)nrhs * DOT_BLOCKS * VGROUP + sizeof(double2) * nrhs * ld +
-                   sizeof(double) * nrhs + 256 * 8;
+                   sizeof(double2) * (size_t)nrhs * DOT_BLOCKS * VGROUP + small + 16 * 256;
     DevBuf &ws = P->gmres_ws; // kept across solves: sized by the largest solve so far
     SPM_TRY(ws.ensure(bytes));
     char *p = ws.as<char>();
@@ -369,7 +406,20 @@ spm_status solve_typed(spm_problem_s *P, int mode, const double2 *g, double2 *x,
     C *tmp = reinterpret_cast<C *>(p); p += sizeof(C) * vstride;
     double2 *partial = reinterpret_cast<double2 *>(p); p += sizeof(double2) * nrhs * DOT_BLOCKS * VGROUP;
     double2 *hdev = reinterpret_cast<double2 *>(p); p += sizeof(double2) * nrhs * ld;
-    double *sdev = reinterpret_cast<double *>(p);
+    double2 *h2dev = reinterpret_cast<double2 *>(p); p += sizeof(double2) * nrhs * ld;
+    double2 *nndev = reinterpret_cast<double2 *>(p); p += sizeof(double2) * nrhs * ld;
+    GmresSmall gs;
+    gs.H = reinterpret_cast<double2 *>(p); p += sizeof(double2) * (size_t)nrhs * (restart + 1) * restart;
+    gs.cs = reinterpret_cast<double2 *>(p); p += sizeof(double2) * (size_t)nrhs * restart;
+    gs.sn = reinterpret_cast<double2 *>(p); p += sizeof(double2) * (size_t)nrhs * restart;
+    gs.g = reinterpret_cast<double2 *>(p); p += sizeof(double2) * (size_t)nrhs * (restart + 1);
+    gs.beta = reinterpret_cast<double *>(p); p += sizeof(double) * nrhs;
+    gs.rtol = reinterpret_cast<double *>(p); p += sizeof(double) * nrhs;
+    double *sdev = reinterpret_cast<double *>(p); p += sizeof(double) * nrhs;
+    gs.scale = sdev;
+    gs.active = reinterpret_cast<int *>(p); p += sizeof(int) * nrhs;
+    gs.count = reinterpret_cast<int *>(p);
+    int count_host[2] = {0, 0};
 
     std::vector<double> gnorm, rnorm, rtol(nrhs), scl(nrhs);
     SPM_TRY(norms<double2>(g, N, nrhs, partial, hdev, ld, gnorm, s));
@@ -404,7 +454,9 @@ spm_status solve_typed(spm_problem_s *P, int mode, const double2 *g, double2 *x,
         SPM_CUDA_TRY(cudaMemcpyAsync(rin, tmp, sizeof(C) * vstride, cudaMemcpyDeviceToDevice, s));
         int it_cycle = 0;
         int cyc_restart = restart < maxit - iters ? restart : maxit - iters;
-        SPM_TRY(gmres_cycle<R>(P, inner_prec, rin, d, nrhs, cyc_restart, rtol, V, tmp, partial, hdev, sdev, &it_cycle, s));
+        SPM_CUDA_TRY(cudaMemcpyAsync(gs.rtol, rtol.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
+        SPM_TRY(gmres_cycle<R>(P, inner_prec, rin, d, nrhs, cyc_restart, V, tmp, partial, hdev, h2dev, nndev, gs,
+                               count_host, &it_cycle, s));
         iters += it_cycle;
         ++outer;
         for (int b = 0; b < nrhs; ++b) scl[b] = rtol[b] < 1e299 ? rnorm[b] : 0.0;

@@ -19,14 +19,12 @@
 //   forward (deepest level first): [y; t] = G w_own, w_own = y, w_bnd -= t
 //   backward (root first):         w_own -= X w_bnd.
 // Nodes of one level have disjoint own unknowns; their boundaries lie on
-// shallower separators, so one launch handles a whole level.  The factor
-// phase uses cuSOLVER getrf/getrs and cuBLAS gemm on the dense fronts;
+// shallower separators, so one launch handles a whole level.  Dense front
+// work (dense.cu): F11^{-1} by Gauss-Jordan with partial pivoting, then
+// X = F11^{-1} F12, F21 F11^{-1} and the update F22 - F21 X as complex GEMMs;
 // assembly, extend-add, the batched level GEMVs, gathers and scatters are
 // kernels here.
-#include <cublas_v2.h>
-#include <cuComplex.h>
 #include <cuda_fp16.h>
-#include <cusolverDn.h>
 
 #include <algorithm>
 #include <atomic>
@@ -51,38 +49,6 @@ struct Node {
     long piv_off = 0;        // pivots
     long scale_off = 0;      // per-column scales of G then X (half storage)
     int depth = 0;
-};
-
-template <typename R> struct blas_t;
-template <> struct blas_t<float> {
-    using C = cuComplex;
-    static cusolverStatus_t getrf_ws(cusolverDnHandle_t h, int n, C *A, int lda, int *lw)
-    { return cusolverDnCgetrf_bufferSize(h, n, n, A, lda, lw); }
-    static cusolverStatus_t getrf(cusolverDnHandle_t h, int n, C *A, int lda, C *ws, int *piv, int *info)
-    { return cusolverDnCgetrf(h, n, n, A, lda, ws, piv, info); }
-    static cusolverStatus_t getrs(cusolverDnHandle_t h, int n, int nrhs, const C *A, int lda, const int *piv, C *B,
-                                  int ldb, int *info)
-    { return cusolverDnCgetrs(h, CUBLAS_OP_N, n, nrhs, A, lda, piv, B, ldb, info); }
-    static cublasStatus_t gemm(cublasHandle_t h, int m, int n, int k, C alpha, const C *A, int lda, const C *B, int ldb,
-                               C beta, C *Cm, int ldc)
-    { return cublasCgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, m, n, k, &alpha, A, lda, B, ldb, &beta, Cm, ldc); }
-    static C one() { return make_cuComplex(1.f, 0.f); }
-    static C mone() { return make_cuComplex(-1.f, 0.f); }
-};
-template <> struct blas_t<double> {
-    using C = cuDoubleComplex;
-    static cusolverStatus_t getrf_ws(cusolverDnHandle_t h, int n, C *A, int lda, int *lw)
-    { return cusolverDnZgetrf_bufferSize(h, n, n, A, lda, lw); }
-    static cusolverStatus_t getrf(cusolverDnHandle_t h, int n, C *A, int lda, C *ws, int *piv, int *info)
-    { return cusolverDnZgetrf(h, n, n, A, lda, ws, piv, info); }
-    static cusolverStatus_t getrs(cusolverDnHandle_t h, int n, int nrhs, const C *A, int lda, const int *piv, C *B,
-                                  int ldb, int *info)
-    { return cusolverDnZgetrs(h, CUBLAS_OP_N, n, nrhs, A, lda, piv, B, ldb, info); }
-    static cublasStatus_t gemm(cublasHandle_t h, int m, int n, int k, C alpha, const C *A, int lda, const C *B, int ldb,
-                               C beta, C *Cm, int ldc)
-    { return cublasZgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, m, n, k, &alpha, A, lda, B, ldb, &beta, Cm, ldc); }
-    static C one() { return make_cuDoubleComplex(1.0, 0.0); }
-    static C mone() { return make_cuDoubleComplex(-1.0, 0.0); }
 };
 
 // ---------------------------------------------------------------- kernels
@@ -153,46 +119,6 @@ template <typename C> __global__ void k_identity(C *a, int n, int ld)
     int r = (int)(gid % n), c = (int)(gid / n);
     a[(long)c * ld + r].x = r == c ? 1 : 0;
     a[(long)c * ld + r].y = 0;
-}
-
-// Static pivot perturbation.  Pivoting stays inside each front's fully summed
-// block F11, so a box of the dissection whose part of S is (nearly) singular
-// leaves tiny pivots in U even when S is well conditioned, and every later
-// Schur complement then carries their reciprocal.  After the partial-pivoting
-// LU of F11, each |U_ii| below tau * max_j |U_jj| is raised to that size, phase
-// kept: the factor becomes exact for S plus a perturbation of rank equal to the
-// number of raised pivots (counted in *count), which GMRES on the
-// preconditioned system absorbs in about that many extra iterations.
-template <typename C> __global__ void __launch_bounds__(1024) k_perturb_pivots(C *lu, int ld, int nd, double tau, int *count)
-{
-    __shared__ double red[32];
-    double mx = 0;
-    for (int i = threadIdx.x; i < nd; i += blockDim.x) {
-        const C u = lu[(long)i * ld + i];
-        mx = fmax(mx, sqrt((double)u.x * u.x + (double)u.y * u.y));
-    }
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        mx = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (threadIdx.x == 0) red[0] = mx;
-    }
-    __syncthreads();
-    const double floor_ = tau * red[0];
-    int raised = 0;
-    for (int i = threadIdx.x; i < nd; i += blockDim.x) {
-        C &u = lu[(long)i * ld + i];
-        const double a = sqrt((double)u.x * u.x + (double)u.y * u.y);
-        if (a < floor_) {
-            const double sx = a > 0 ? u.x / a : 1.0, sy = a > 0 ? u.y / a : 0.0;
-            u.x = (decltype(u.x))(floor_ * sx);
-            u.y = (decltype(u.y))(floor_ * sy);
-            ++raised;
-        }
-    }
-    if (raised) atomicAdd(count, raised);
 }
 
 // Level tables.  Per node of a level: its matrix (rows x cols, column-major,
@@ -398,12 +324,10 @@ struct NDFactor {
     std::vector<Level> levels;
     DevBuf lv_nodes, lv_units, lv_tiles;
     long max_pack_in = 0, max_pack_out = 0;
-    cublasHandle_t cublas = nullptr;
-    cusolverDnHandle_t cusolver = nullptr;
+    DenseWork *dense = nullptr; // Gauss-Jordan workspace
     ~NDFactor()
     {
-        if (cublas) cublasDestroy(cublas);
-        if (cusolver) cusolverDnDestroy(cusolver);
+        spm_dense_work_free(dense);
         pts.release(); maps.release(); rels.release(); fac.release(); piv.release();
         front.release(); stack.release(); work.release(); info.release(); solve_ws.release();
         lv_nodes.release(); lv_units.release(); lv_tiles.release(); scales.release();
@@ -412,11 +336,6 @@ struct NDFactor {
 
 void spm_factor_free(NDFactor *f) { delete f; }
 
-namespace {
-std::atomic<int> g_factor_gemm(0);
-}
-int spm_factor_gemm_mode() { return g_factor_gemm.load(); }
-void spm_set_factor_gemm_mode(int m) { g_factor_gemm.store(m); }
 
 namespace {
 
@@ -473,8 +392,7 @@ int build_tree(std::vector<Node> &nodes, const int lo[3], const int hi[3], int v
 template <typename R>
 static spm_status factor_typed(spm_problem_s *P, NDFactor *F, bool half_store, int variant)
 {
-    using BT = blas_t<R>;
-    using C = typename BT::C;
+    using C = typename cplx_of<R>::type;
     using CV = typename cplx_of<R>::type;
     const int n = P->n;
     const long n3 = (long)n * n * n;
@@ -577,30 +495,16 @@ static spm_status factor_typed(spm_problem_s *P, NDFactor *F, bool half_store, i
         SPM_TRY(gx.ensure(sizeof(C) * max_gx));
         SPM_TRY(F->scales.ensure(sizeof(float) * scale_total));
     }
-    SPM_TRY(F->piv.ensure(sizeof(int) * std::max<long>(piv_total, 1)));
     SPM_TRY(F->front.ensure(sizeof(C) * max_f * max_f));
     SPM_TRY(F->stack.ensure(sizeof(C) * std::max<size_t>(max_upd_stack, 1)));
-    SPM_TRY(F->info.ensure(sizeof(int) * 3)); // getrf info, getrs info, raised pivots
-    if (!F->cublas && cublasCreate(&F->cublas) != CUBLAS_STATUS_SUCCESS) { spm_set_error("cublasCreate failed"); return SPM_ERR_CUDA; }
-    if (!F->cusolver && cusolverDnCreate(&F->cusolver) != CUSOLVER_STATUS_SUCCESS) { spm_set_error("cusolverDnCreate failed"); return SPM_ERR_CUDA; }
-    cublasSetStream(F->cublas, s);
-    cusolverDnSetStream(F->cusolver, s);
-    // complex64 factors: the Schur-complement GEMMs in plain FP32, or FP32
-    // emulated on the BF16 tensor cores (BF16x9, FP32-level accuracy) when chosen
-    cublasSetMathMode(F->cublas, (sizeof(R) == 4 && spm_factor_gemm_mode() == 1) ? CUBLAS_FP32_EMULATED_BF16X9_MATH
-                                                                               : CUBLAS_DEFAULT_MATH);
-    int lwork = 0;
-    if (BT::getrf_ws(F->cusolver, (int)F->max_own3, F->front.as<C>(), (int)max_f, &lwork) != CUSOLVER_STATUS_SUCCESS) {
-        spm_set_error("getrf buffer size query failed");
-        return SPM_ERR_CUDA;
-    }
-    SPM_TRY(F->work.ensure(sizeof(C) * std::max(lwork, 1)));
+    SPM_TRY(F->info.ensure(sizeof(int) * 3)); // expired grid barrier, unused, raised pivots
+    if (!F->dense) F->dense = spm_dense_work_new();
     SPM_CUDA_TRY(cudaMemsetAsync(F->info.ptr, 0, sizeof(int) * 3, s));
 
     const C *Sdev = reinterpret_cast<const C *>(sizeof(R) == 8 ? P->S128.ptr : P->S64.ptr);
     const int *dpts = F->pts.as<int>(), *dmaps = F->maps.as<int>(), *drels = F->rels.as<int>();
     C *front = F->front.as<C>(), *stack = F->stack.as<C>(), *fac = F->fac.as<C>();
-    int *dpiv = F->piv.as<int>(), *dinfo = F->info.as<int>();
+    int *dinfo = F->info.as<int>();
     std::vector<size_t> upd_pos(NN, 0);
     size_t top = 0;
     for (int id = 0; id < NN; ++id) {
@@ -621,44 +525,21 @@ static spm_status factor_typed(spm_problem_s *P, NDFactor *F, bool half_store, i
         }
         for (int ch : {nd.left, nd.right}) if (ch >= 0) top -= upd_size[ch];
         SPM_CUDA_TRY(cudaGetLastError());
-        // partial factorisation
-        if (BT::getrf(F->cusolver, o3, front, f, F->work.as<C>(), dpiv + nd.piv_off, dinfo) != CUSOLVER_STATUS_SUCCESS) {
-            spm_set_error("getrf failed at node %d", id);
-            return SPM_ERR_CUDA;
-        }
-        if (o3 > 0) k_perturb_pivots<C><<<1, 1024, 0, s>>>(front, f, o3, pivot_floor<R>(), dinfo + 2);
+        // F11^{-1} by Gauss-Jordan (partial pivoting inside the own block, static
+        // pivot floor), then with G = [F11^{-1}; F21 F11^{-1}] (f x o3, ld f) and
+        // X = F11^{-1} F12 (o3 x b3, ld o3) stored after it:
+        //   X = F11^{-1} F12,  G_bottom = F21 F11^{-1},  update = F22 - F21 X.
+        C *G = half_store ? gx.as<C>() : fac + nd.fac_off;
+        SPM_TRY(spm_dense_inverse<C>(o3, front, f, G, f, pivot_floor<R>(), dinfo + 2, dinfo, F->dense, s));
         if (b3 > 0) {
-            if (BT::getrs(F->cusolver, o3, b3, front, f, dpiv + nd.piv_off, front + (long)o3 * f, f, dinfo + 1) !=
-                CUSOLVER_STATUS_SUCCESS) {
-                spm_set_error("getrs failed at node %d", id);
-                return SPM_ERR_CUDA;
-            }
-            // update = F22 - F21 X, in place in the front
-            if (BT::gemm(F->cublas, b3, b3, o3, BT::mone(), front + o3, f, front + (long)o3 * f, f, BT::one(),
-                         front + (long)o3 * f + o3, f) != CUBLAS_STATUS_SUCCESS) {
-                spm_set_error("gemm failed at node %d", id);
-                return SPM_ERR_CUDA;
-            }
+            C *X = G + (long)f * o3;
+            SPM_TRY(spm_dense_gemm<C>(o3, b3, o3, 1.0, G, f, front + (long)o3 * f, f, 0.0, X, o3, s));
+            SPM_TRY(spm_dense_gemm<C>(b3, o3, o3, 1.0, front + o3, f, G, f, 0.0, G + o3, f, s));
+            SPM_TRY(spm_dense_gemm<C>(b3, b3, o3, -1.0, front + o3, f, X, o3, 1.0, front + (long)o3 * f + o3, f, s));
             // push the update
             upd_pos[id] = top;
             k_copy_block<C><<<blocks((long)b3 * b3), 256, 0, s>>>(stack + top, b3, front + (long)o3 * f + o3, f, b3, b3);
             top += upd_size[id];
-        }
-        // persistent: G = [F11^{-1}; F21 F11^{-1}] (f x o3, ld f) then X (o3 x b3, ld o3)
-        C *G = half_store ? gx.as<C>() : fac + nd.fac_off;
-        k_identity<C><<<blocks((long)o3 * o3), 256, 0, s>>>(G, o3, f);
-        if (BT::getrs(F->cusolver, o3, o3, front, f, dpiv + nd.piv_off, G, f, dinfo + 1) != CUSOLVER_STATUS_SUCCESS) {
-            spm_set_error("getrs (inverse) failed at node %d", id);
-            return SPM_ERR_CUDA;
-        }
-        if (b3 > 0) {
-            if (BT::gemm(F->cublas, b3, o3, o3, BT::one(), front + o3, f, G, f, C{0, 0}, G + o3, f) !=
-                CUBLAS_STATUS_SUCCESS) {
-                spm_set_error("gemm (F21 F11^-1) failed at node %d", id);
-                return SPM_ERR_CUDA;
-            }
-            k_copy_block<C><<<blocks((long)o3 * b3), 256, 0, s>>>(G + (long)f * o3, o3, front + (long)o3 * f, f, o3,
-                                                                  b3);
         }
         if constexpr (sizeof(R) == 4) {
             if (half_store) {
@@ -680,11 +561,10 @@ static spm_status factor_typed(spm_problem_s *P, NDFactor *F, bool half_store, i
     SPM_CUDA_TRY(cudaStreamSynchronize(s));
     F->front.release();
     F->stack.release();
-    F->work.release();
     F->raised_pivots = hinfo[2];
-    if (hinfo[0] != 0 || hinfo[1] != 0) {
-        spm_set_error("zero pivot in the multifrontal factor (info %d, %d)", hinfo[0], hinfo[1]);
-        return SPM_ERR_NUMERICAL;
+    if (hinfo[0] != 0) {
+        spm_set_error("a grid barrier of the Gauss-Jordan panel expired (code %d)", hinfo[0]);
+        return SPM_ERR_TIMEOUT;
     }
     // level tables for the batched solve
     {
@@ -759,8 +639,7 @@ static spm_status factor_typed(spm_problem_s *P, NDFactor *F, bool half_store, i
 template <typename R>
 static spm_status solve_typed(spm_problem_s *P, NDFactor *F, const void *bv, void *xv, int nrhs, cudaStream_t s)
 {
-    using BT = blas_t<R>;
-    using C = typename BT::C;
+    using C = typename cplx_of<R>::type;
     const int n = P->n;
     const long n3 = (long)n * n * n;
     C *x = reinterpret_cast<C *>(xv);

@@ -57,12 +57,12 @@ def test_argument_validation_without_gpu(spm):
 
 
 def test_host_side_settings_without_gpu(spm):
-    """Process-wide settings that touch no device: the apply plan table and the
-    factor GEMM mode round-trip, and invalid values are refused."""
+    """Process-wide settings that touch no device: the apply plan table
+    round-trips, and invalid values are refused."""
     lib = spm.lib
     saved = spm.get_apply_plan(spm.SPM_C64, 128)
     try:
-        for z in (spm.ZPASS_FOUR, spm.ZPASS_ONE, spm.ZPASS_TMA, -1):
+        for z in (spm.ZPASS_FOUR, spm.ZPASS_ONE, spm.ZPASS_TMA, spm.ZPASS_E16, spm.ZPASS_STAGED, -1):
             spm.set_apply_plan(spm.SPM_C64, 128, z)
             assert spm.get_apply_plan(spm.SPM_C64, 128) == z
     finally:
@@ -71,13 +71,7 @@ def test_host_side_settings_without_gpu(spm):
     assert lib.spm_set_apply_plan(spm.SPM_C64, 16, spm.ZPASS_TMA) == spm.SPM_ERR_INVALID_ARG  # too short for TMA
     assert lib.spm_set_apply_plan(spm.SPM_C64, 100, spm.ZPASS_ONE) == spm.SPM_ERR_INVALID_ARG  # no such length
     assert lib.spm_set_apply_plan(spm.SPM_MIXED, 128, spm.ZPASS_ONE) == spm.SPM_ERR_INVALID_ARG
-    mode = spm.get_factor_gemm()
-    try:
-        spm.set_factor_gemm(1)
-        assert spm.get_factor_gemm() == 1
-    finally:
-        spm.set_factor_gemm(mode)
-    assert lib.spm_set_factor_gemm(2) == spm.SPM_ERR_INVALID_ARG
+    assert lib.spm_set_apply_plan(spm.SPM_C64, 128, 5) == spm.SPM_ERR_INVALID_ARG  # no such variant
     rep = spm.FactorReport()
     assert lib.spm_factor_info(None, spm.SPM_C64, ctypes.byref(rep)) == spm.SPM_ERR_INVALID_ARG
     assert lib.spm_device_status(None) == spm.SPM_ERR_INVALID_ARG

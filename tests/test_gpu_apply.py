@@ -209,11 +209,30 @@ def test_every_zpass_kernel_matches_oracle(spm, n):
     cp.async prefetch, persistent TMA-fed) gives the same apply: complex128 to
     1e-12 and complex64 to 2e-5 of the FP64 oracle, for one and three
     right-hand sides; no bounded device wait gives up."""
+    _check_zpass_variants(spm, n, (1, 3))
+
+
+def _zpass_variants(spm, L):
+    if L in (96, 192):
+        return [spm.ZPASS_ONE, spm.ZPASS_TMA, spm.ZPASS_STAGED]
+    v = [spm.ZPASS_FOUR, spm.ZPASS_ONE, spm.ZPASS_TMA, spm.ZPASS_STAGED] if L >= 32 else [spm.ZPASS_FOUR]
+    if L in (128, 256, 512):
+        v.append(spm.ZPASS_E16)
+    if L in (64, 128):  # the same z-pass kernels with the x and y passes fused per plane
+        v += [z | spm.PLAN_FUSED_XY for z in list(v)]
+    return v
+
+
+def test_every_zpass_kernel_n128(spm):
+    """The z-pass kernels at L = 256 (n = 128), one right-hand side."""
+    _check_zpass_variants(spm, 128, (1,))
+
+
+def _check_zpass_variants(spm, n, rhs_counts):
     L = 2 * n
-    variants = [spm.ZPASS_ONE, spm.ZPASS_TMA] if L in (96, 192) else \
-        ([spm.ZPASS_FOUR, spm.ZPASS_ONE, spm.ZPASS_TMA] if L >= 32 else [spm.ZPASS_FOUR])
+    variants = _zpass_variants(spm, L)
     P, k, m, p = make(spm, n, "bumps", seed=n)
-    for nrhs in (1, 3):
+    for nrhs in rhs_counts:
         x = si.random_field(n, 300 + n, nrhs)
         ref = oracle.apply_fft(n, k, m, p, x)
         for prec, dtype, tol in ((spm.SPM_C128, torch.complex128, 1e-12), (spm.SPM_C64, torch.complex64, 2e-5)):
@@ -230,6 +249,9 @@ def test_every_zpass_kernel_matches_oracle(spm, n):
                     assert spm.get_apply_plan(prec, L) == z
             finally:
                 spm.set_apply_plan(prec, L, saved)
+
+
+def test_apply_plan_rejects_unknown_variants(spm):
     with pytest.raises(spm.SpmError):
         spm.set_apply_plan(spm.SPM_C64, 96, spm.ZPASS_FOUR)
     with pytest.raises(spm.SpmError):
@@ -260,3 +282,48 @@ def test_apply_Q_ragged_tiles_random_stencils(spm, n):
     print(f"n={n}: Q c128 {e128:.2e}, c64 {e64:.2e}")
     assert e128 < 1e-14
     assert e64 < 5e-6
+
+
+@pytest.mark.parametrize("n,nrhs", [(16, 2), (64, 1)])
+def test_apply_A_cufft_comparison_matches_oracle(spm, n, nrhs):
+    """The cuFFT comparison apply (spm_apply_A_cufft: full padded 3-D transforms)
+    computes the same operator: complex128 to 1e-12 and complex64 to 2e-5."""
+    P, k, m, p = make(spm, n, "bumps", seed=n)
+    x = si.random_field(n, 500 + n, nrhs)
+    ref = oracle.apply_fft(n, k, m, p, x)
+    for dtype, tol in ((torch.complex128, 1e-12), (torch.complex64, 2e-5)):
+        y = torch.zeros(x.shape, dtype=dtype, device="cuda")
+        P.apply_A_cufft(to_dev(x, dtype), y)
+        torch.cuda.synchronize()
+        e = rel(y.cpu().numpy().astype(np.complex128), ref)
+        print(f"cuFFT apply n={n} {dtype}: rel err {e:.2e}")
+        assert e < tol
+
+
+def test_apply_plans_persist_as_json(spm, tmp_path):
+    """The autotuner's choices round-trip through spm_save_apply_plans /
+    spm_load_apply_plans; a file tuned on another device is refused."""
+    import json
+    saved = {(pr, L): spm.get_apply_plan(pr, L) for pr in (spm.SPM_C64, spm.SPM_C128) for L in (64, 128)}
+    try:
+        spm.set_apply_plan(spm.SPM_C64, 128, spm.ZPASS_E16)
+        spm.set_apply_plan(spm.SPM_C128, 64, spm.ZPASS_ONE)
+        path = tmp_path / "plans.json"
+        spm.save_apply_plans(str(path))
+        doc = json.loads(path.read_text())
+        assert doc["device"] == torch.cuda.get_device_name(0)
+        entries = {(e["prec"], e["L"]): e["variant"] for e in doc["plans"]}
+        assert entries[("c64", 128)] == spm.ZPASS_E16 and entries[("c128", 64)] == spm.ZPASS_ONE
+        spm.set_apply_plan(spm.SPM_C64, 128, -1)
+        spm.set_apply_plan(spm.SPM_C128, 64, -1)
+        assert spm.load_apply_plans(str(path)) >= 2
+        assert spm.get_apply_plan(spm.SPM_C64, 128) == spm.ZPASS_E16
+        assert spm.get_apply_plan(spm.SPM_C128, 64) == spm.ZPASS_ONE
+        doc["device"] = "some other GPU"
+        other = tmp_path / "other.json"
+        other.write_text(json.dumps(doc))
+        with pytest.raises(spm.SpmError):
+            spm.load_apply_plans(str(other))
+    finally:
+        for (pr, L), z in saved.items():
+            spm.set_apply_plan(pr, L, z)

@@ -34,11 +34,19 @@ def test_n256_apply_on_sampled_points(spm):
     idx = [lin(0, 0, 0), lin(n - 1, n - 1, n - 1), lin(0, 0, n // 3), lin(n // 2, 0, n // 5),
            lin(n // 2, n // 2, n // 2)] + [int(v) for v in rng.integers(0, n ** 3, 3)]
     ref = oracle.apply_direct_points(n, k, m, p, x, idx)  # (8, 3)
-    for dtype, tol in ((torch.complex64, 2e-5), (torch.complex128, 1e-12)):
-        y = torch.zeros(x.shape, dtype=dtype, device="cuda")
-        P.apply_A(torch.from_numpy(x).to(dtype).to("cuda"), y)
-        P.device_status()
-        got = y.reshape(3, -1)[:, torch.tensor(idx, device="cuda")].T.cpu().numpy().astype(np.complex128)
-        e = np.linalg.norm(got - ref) / np.linalg.norm(ref)
-        print(f"n=256 {dtype}: sampled rel err {e:.2e}")
-        assert e < tol
+    L = 2 * n
+    for dtype, tol, prec in ((torch.complex64, 2e-5, spm.SPM_C64), (torch.complex128, 1e-12, spm.SPM_C128)):
+        saved = spm.get_apply_plan(prec, L)
+        try:
+            # every z-pass kernel of this length (the bench uses the fastest)
+            for z in (spm.ZPASS_FOUR, spm.ZPASS_ONE, spm.ZPASS_TMA, spm.ZPASS_E16, spm.ZPASS_STAGED):
+                spm.set_apply_plan(prec, L, z)
+                y = torch.zeros(x.shape, dtype=dtype, device="cuda")
+                P.apply_A(torch.from_numpy(x).to(dtype).to("cuda"), y)
+                P.device_status()
+                got = y.reshape(3, -1)[:, torch.tensor(idx, device="cuda")].T.cpu().numpy().astype(np.complex128)
+                e = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+                print(f"n=256 {dtype} z-pass {z}: sampled rel err {e:.2e}")
+                assert e < tol, (z, e)
+        finally:
+            spm.set_apply_plan(prec, L, saved)
