@@ -751,6 +751,35 @@ def run_ours(args):
             "gpu_launches": launches_per_step * args.steps * max(1, -(-nrhs // chunk_of(P, n, args.prec))),
             "clocks": clocks,
             "step_ms_min": float(np.min(step_ms)), "step_ms_median": float(np.median(step_ms))}
+    if nrhs == 1:
+        # every pass of one apply timed with CUDA events on the launch stream
+        # (serialised: an event between passes), and the dominant pass's own
+        # roofline: its algorithmic flops over its measured time
+        pass_ms = P.profile_apply(x, y, with_q=(args.op == "QA"), reps=50 if n <= 64 else 5)
+        zv = spm.get_apply_plan(spm.SPM_C64 if args.prec == "c64" else spm.SPM_C128, 2 * n)
+        names = (["xy-forward (fused)", "z-pass", "yx-inverse (fused)"] if zv >= 0 and zv & 8
+                 else ["x-forward", "y-forward", "z-pass", "y-inverse", "x-inverse"])
+        if args.op == "QA":
+            names = names + ["Q"]
+        L = 2 * n
+        # z-pass: 7 full-length line transforms per column (4 forward, 3 inverse) over L^2
+        # columns at 5 L log2 L each, plus 6 complex MACs (48 flops) per frequency
+        z_flops = 7.0 * L * L * 5.0 * L * np.log2(L) + 48.0 * L ** 3
+        q_flops = 1944.0 * n ** 3
+        tot = sum(pass_ms)
+        line["passes"] = {"names": names, "ms": pass_ms, "share": [v / tot for v in pass_ms],
+                          "note": "serialised by an event between passes; the pipelined step is shorter"}
+        iz = names.index("z-pass")
+        fpk = fpeak * 1e12
+        line["roofline"]["z_pass"] = {"kernel": "z-pass (" + zpass_name(spm, args.prec, L) + ")", "bound": "alu",
+                                      "ms": pass_ms[iz], "algorithmic_flops": z_flops,
+                                      "achieved": z_flops / (pass_ms[iz] / 1000.0) / 1e12, "peak": fpeak,
+                                      "unit": "TFLOP/s", "frac": z_flops / (pass_ms[iz] / 1000.0) / fpk}
+        if args.op == "QA":
+            line["roofline"]["q_gather"] = {"kernel": "k_q", "bound": "alu", "ms": pass_ms[-1],
+                                            "algorithmic_flops": q_flops,
+                                            "achieved": q_flops / (pass_ms[-1] / 1000.0) / 1e12, "peak": fpeak,
+                                            "unit": "TFLOP/s", "frac": q_flops / (pass_ms[-1] / 1000.0) / fpk}
     if args.prec == "c64" and nrhs == 1:
         # the apply of A alone, hand-written passes against the cuFFT comparison apply
         a_ms = time_apply(torch, P.apply_A, x, y, 200 if n <= 64 else 20)

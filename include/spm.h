@@ -233,6 +233,17 @@ spm_status spm_solve_S(spm_problem prob, spm_prec prec, const void *b_dev, void 
 spm_status spm_get_apply_plan(spm_prec prec, int L, int *zvariant);
 spm_status spm_set_apply_plan(spm_prec prec, int L, int zvariant);
 
+/* Device time of every pass of one apply of A (with_q = 0) or Q A (with_q = 1)
+ * to one right-hand side (x_dev, y_dev as in spm_apply_A), averaged over reps
+ * applies, in launch order: x-forward, y-forward, z-pass, y-inverse, x-inverse
+ * (or, with the plan's fused plane passes: xy-forward, z-pass, yx-inverse),
+ * then Q.  An event is recorded after every pass, so the passes run
+ * serialised and their sum exceeds the pipelined time of spm_apply_A.
+ * pass_ms: at least 7 floats; *npasses receives the count.  The paper has no
+ * counterpart (measurement only).  Synchronises `stream`. */
+spm_status spm_profile_apply(spm_problem prob, spm_prec prec, const void *x_dev, void *y_dev, int with_q,
+                             int reps, float *pass_ms, int *npasses, void *stream);
+
 /* The autotuner's choices persisted as JSON: {"device": name, "plans": [{"prec":
  * "c64" | "c128", "L": length, "variant": v, "ms": [per-apply ms of variants
  * 0..4 when they were timed, else 0], "fused_xy_ms": ms of the best variant with

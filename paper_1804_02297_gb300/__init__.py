@@ -28,7 +28,7 @@ EXPORTS = [
     "spm_lattice_constant", "spm_last_error", "spm_apply_A_noalloc",
     "spm_create_batch", "spm_destroy_batch", "spm_batch_size", "spm_batch_problem", "spm_batch_build_stencils",
     "spm_batch_apply_A", "spm_batch_solve", "spm_measure_peak", "spm_apply_A_cufft",
-    "spm_save_apply_plans", "spm_load_apply_plans",
+    "spm_save_apply_plans", "spm_load_apply_plans", "spm_profile_apply",
 ]
 
 
@@ -100,6 +100,7 @@ def _load():
         "spm_apply_A_noalloc": [P, I, P, P, I, P],
         "spm_apply_A_cufft": [P, I, P, P, I, P],
         "spm_save_apply_plans": [ctypes.c_char_p],
+        "spm_profile_apply": [P, I, P, P, I, I, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(I), P],
         "spm_load_apply_plans": [ctypes.c_char_p, ctypes.POINTER(I)],
         "spm_apply_QA": [P, I, P, P, I, P],
         "spm_apply_Q": [P, I, P, P, I, P],
@@ -243,6 +244,14 @@ class Problem:
         """y = A x through cuFFT 3-D transforms (comparison path, not the hot path)."""
         _check(lib.spm_apply_A_cufft(self.h, _prec_of(x), _ptr(x), _ptr(y), _nrhs(x, self.n), _stream(stream)))
         return y
+
+    def profile_apply(self, x, y, with_q=True, reps=20, stream=None):
+        """Per-pass device ms of one apply (serialised passes): list in launch order."""
+        ms = (ctypes.c_float * 8)()
+        k = ctypes.c_int()
+        _check(lib.spm_profile_apply(self.h, _prec_of(x), _ptr(x), _ptr(y), int(with_q), int(reps), ms,
+                                     ctypes.byref(k), _stream(stream)))
+        return [ms[i] for i in range(k.value)]
 
     def apply_QA(self, x, y, stream=None):
         _check(lib.spm_apply_QA(self.h, _prec_of(x), _ptr(x), _ptr(y), _nrhs(x, self.n), _stream(stream)))

@@ -335,6 +335,15 @@ extern "C" spm_status spm_set_apply_plan(spm_prec prec, int L, int zvariant)
     return spm_apply_plan_impl(prec, L, nullptr, &zvariant);
 }
 
+extern "C" spm_status spm_profile_apply(spm_problem P, spm_prec prec, const void *x, void *y, int with_q, int reps,
+                                        float *pass_ms, int *npasses, void *stream)
+{
+    SPM_TRY(check_apply(P, prec, x, y, 1));
+    if (!pass_ms || !npasses || reps < 1) { spm_set_error("pass_ms, npasses must be non-NULL and reps >= 1"); return SPM_ERR_INVALID_ARG; }
+    if (with_q && !P->have_stencils) { spm_set_error("stencils not built"); return SPM_ERR_NOT_BUILT; }
+    return spm_profile_apply_impl(P, prec, x, y, with_q != 0, reps, pass_ms, npasses, as_stream(stream));
+}
+
 extern "C" spm_status spm_save_apply_plans(const char *path)
 {
     if (!path) { spm_set_error("NULL path"); return SPM_ERR_INVALID_ARG; }

@@ -988,13 +988,18 @@ spm_status launch_ztma(typename cplx_of<R>::type *W2, const typename cplx_of<R>:
 }
 
 
+// ev (may be NULL): events recorded after each pass on s, so that the caller can
+// time every pass of one apply (spm_profile_apply); *nev counts them.
 template <typename R, int L>
 spm_status apply_chunk_v2(const typename cplx_of<R>::type *xb, typename cplx_of<R>::type *yb,
                     const typename cplx_of<R>::type *m, const typename cplx_of<R>::type *p,
                     const typename cplx_of<R>::type *spec, const typename cplx_of<R>::type *tw,
                     typename cplx_of<R>::type *W1, typename cplx_of<R>::type *W2, int nb, int zvar, int *err,
-                    cudaStream_t s)
+                    cudaStream_t s, cudaEvent_t *ev = nullptr, int *nev = nullptr)
 {
+    auto mark = [&]() {
+        if (ev) cudaEventRecord(ev[(*nev)++], s);
+    };
     using C = typename cplx_of<R>::type;
     constexpr int n = L / 2, T = L / line_elems(L), TX = tx_of<R, L>::v;
     constexpr int LPB = 256 / T > 0 ? 256 / T : 1;
@@ -1029,6 +1034,7 @@ spm_status apply_chunk_v2(const typename cplx_of<R>::type *xb, typename cplx_of<
                 axy = true;
             }
             launch_pdl(k2_xyfwd<R, L>, dim3(n, 4, nb), dim3(256), xyf<R, L>::smem, s, xb, m, p, W2, tw);
+            mark();
             fused_done = true;
         }
     }
@@ -1036,12 +1042,14 @@ spm_status apply_chunk_v2(const typename cplx_of<R>::type *xb, typename cplx_of<
         long rows = (long)nb * n2;
         launch_pdl(k2_xfwd<R, L>, dim3((unsigned)((rows + LPB - 1) / LPB)), dim3(LPB * T), sm_rows, s, xb, m, p, W1,
                    (int)rows, tw);
+        mark();
         if constexpr (line_elems(L) == 8 && n % 2 == 0)
             launch_pdl(k2_cols2<R, L, -1, true>, dim3(L / TX, n / 2, nb * 4), dim3(THR), 2 * sm_cols, s, (const C *)W1,
                        W2, L, (long)L, 4, 4 * n2 * L, n2 * L, n * (long)L, 4 * (long)n * L2, (long)n * L2, L2, tw);
         else
             launch_pdl(k2_cols<R, L, -1, true>, dim3(L / TX, n, nb * 4), dim3(THR), sm_cols, s, (const C *)W1, W2, L,
                        (long)L, 4, 4 * n2 * L, n2 * L, n * (long)L, 4 * (long)n * L2, (long)n * L2, L2, tw);
+        mark();
     }
     bool done = false;
     if constexpr (L >= 32) {
@@ -1082,9 +1090,11 @@ spm_status apply_chunk_v2(const typename cplx_of<R>::type *xb, typename cplx_of<
         }
     }
     if (!done) launch_pdl(k2_zprod1<R, L>, dim3((unsigned)(L2 / TX), nb), dim3(THR), sm_zprod, s, W2, spec, tw);
+    mark();
     if (fused_done) {
         if constexpr (L == 64 || L == 128)
             launch_pdl(k2_yxinv<R, L>, dim3(n, 3, nb), dim3(256), xyf<R, L>::smem, s, (const C *)W2, xb, yb, tw);
+        mark();
         return SPM_OK;
     }
     if constexpr (line_elems(L) == 8 && n % 2 == 0)
@@ -1093,11 +1103,13 @@ spm_status apply_chunk_v2(const typename cplx_of<R>::type *xb, typename cplx_of<
     else
         launch_pdl(k2_cols<R, L, 1, false>, dim3(L / TX, n, nb * 3), dim3(THR), sm_cols, s, (const C *)W2, W1, n,
                    (long)L, 3, 4 * (long)n * L2, (long)n * L2, L2, 3 * n2 * L, n2 * L, n * (long)L, tw);
+    mark();
     {
         long rows = (long)nb * 3 * n2;
         launch_pdl(k2_xinv<R, L>, dim3((unsigned)((rows + LPB - 1) / LPB)), dim3(LPB * T), sm_rows, s, (const C *)W1,
                    xb, yb, rows, tw);
     }
+    mark();
     return SPM_OK;
 }
 
@@ -1106,18 +1118,18 @@ spm_status run_chunk(int L, const typename cplx_of<R>::type *xb, typename cplx_o
                      const typename cplx_of<R>::type *m, const typename cplx_of<R>::type *p,
                      const typename cplx_of<R>::type *spec, const typename cplx_of<R>::type *tw,
                      typename cplx_of<R>::type *W1, typename cplx_of<R>::type *W2, int nb, int zvar, int *err,
-                     cudaStream_t s)
+                     cudaStream_t s, cudaEvent_t *ev = nullptr, int *nev = nullptr)
 {
     switch (L) {
-    case 8: return apply_chunk_v2<R, 8>(xb, yb, m, p, spec, tw, W1, W2, nb, zvar, err, s);
-    case 16: return apply_chunk_v2<R, 16>(xb, yb, m, p, spec, tw, W1, W2, nb, zvar, err, s);
-    case 32: return apply_chunk_v2<R, 32>(xb, yb, m, p, spec, tw, W1, W2, nb, zvar, err, s);
-    case 64: return apply_chunk_v2<R, 64>(xb, yb, m, p, spec, tw, W1, W2, nb, zvar, err, s);
-    case 128: return apply_chunk_v2<R, 128>(xb, yb, m, p, spec, tw, W1, W2, nb, zvar, err, s);
-    case 256: return apply_chunk_v2<R, 256>(xb, yb, m, p, spec, tw, W1, W2, nb, zvar, err, s);
-    case 512: return apply_chunk_v2<R, 512>(xb, yb, m, p, spec, tw, W1, W2, nb, zvar, err, s);
-    case 96: return apply_chunk_v2<R, 96>(xb, yb, m, p, spec, tw, W1, W2, nb, zvar, err, s);
-    case 192: return apply_chunk_v2<R, 192>(xb, yb, m, p, spec, tw, W1, W2, nb, zvar, err, s);
+    case 8: return apply_chunk_v2<R, 8>(xb, yb, m, p, spec, tw, W1, W2, nb, zvar, err, s, ev, nev);
+    case 16: return apply_chunk_v2<R, 16>(xb, yb, m, p, spec, tw, W1, W2, nb, zvar, err, s, ev, nev);
+    case 32: return apply_chunk_v2<R, 32>(xb, yb, m, p, spec, tw, W1, W2, nb, zvar, err, s, ev, nev);
+    case 64: return apply_chunk_v2<R, 64>(xb, yb, m, p, spec, tw, W1, W2, nb, zvar, err, s, ev, nev);
+    case 128: return apply_chunk_v2<R, 128>(xb, yb, m, p, spec, tw, W1, W2, nb, zvar, err, s, ev, nev);
+    case 256: return apply_chunk_v2<R, 256>(xb, yb, m, p, spec, tw, W1, W2, nb, zvar, err, s, ev, nev);
+    case 512: return apply_chunk_v2<R, 512>(xb, yb, m, p, spec, tw, W1, W2, nb, zvar, err, s, ev, nev);
+    case 96: return apply_chunk_v2<R, 96>(xb, yb, m, p, spec, tw, W1, W2, nb, zvar, err, s, ev, nev);
+    case 192: return apply_chunk_v2<R, 192>(xb, yb, m, p, spec, tw, W1, W2, nb, zvar, err, s, ev, nev);
     default: spm_set_error("unsupported FFT length %d", L); return SPM_ERR_INVALID_ARG;
     }
 }
@@ -1722,6 +1734,75 @@ spm_status spm_load_plans_impl(const char *path, int *loaded)
     }
     if (loaded) *loaded = count;
     return SPM_OK;
+}
+
+// Per-pass device times of one apply (A, or Q A), averaged over reps applies:
+// an event after every pass, so the passes run serialised (no overlap of one
+// pass's tail with the next one's start) and their sum exceeds the pipelined
+// apply time.
+namespace {
+template <typename R>
+spm_status profile_typed(spm_problem_s *P, const void *xv, void *yv, int with_q, int reps, float *pass_ms, int *npasses,
+                         cudaStream_t s)
+{
+    using C = typename cplx_of<R>::type;
+    const int n = P->n, L = P->L;
+    const long n2 = (long)n * n, L2 = (long)L * L;
+    const bool dbl = sizeof(R) == 8;
+    const C *m = dbl ? P->m128.as<C>() : P->m64.as<C>();
+    const C *p = dbl ? P->p128.as<C>() : P->p64.as<C>();
+    const C *spec = dbl ? P->spec128.as<C>() : P->spec64.as<C>();
+    const C *tw = dbl ? P->tw128.as<C>() : P->tw64.as<C>();
+    const int chunk = dbl ? P->chunk128 : P->chunk64;
+    const long w1 = 4 * n2 * L, w2 = 4 * (long)n * L2;
+    SPM_TRY(P->work.ensure(sizeof(C) * (size_t)chunk * (w1 + w2)));
+    C *W1 = P->work.as<C>();
+    C *W2 = W1 + (long)chunk * w1;
+    const C *x = reinterpret_cast<const C *>(xv);
+    C *y = reinterpret_cast<C *>(yv);
+    C *ax = y;
+    if (with_q) {
+        SPM_TRY(P->kry.ensure(std::max(P->kry.bytes, sizeof(C) * 3 * (size_t)n2 * n)));
+        ax = P->kry.as<C>();
+    }
+    int zvar = ZPROD_FOUR;
+    SPM_TRY(choose_zplan<R>(L, x, ax, m, p, spec, tw, W1, W2, 1, P->dev_err.as<int>(), s, &zvar));
+    cudaEvent_t ev[8];
+    for (int k = 0; k < 8; ++k) SPM_CUDA_TRY(cudaEventCreate(&ev[k]));
+    float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int nev = 0;
+    spm_status st = SPM_OK;
+    for (int r = 0; r < reps && st == SPM_OK; ++r) {
+        nev = 0;
+        cudaEventRecord(ev[nev++], s);
+        st = run_chunk<R>(L, x, ax, m, p, spec, tw, W1, W2, 1, zvar, P->dev_err.as<int>(), s, ev, &nev);
+        if (st == SPM_OK && with_q) {
+            st = spm_apply_Q_impl(P, dbl ? SPM_C128 : SPM_C64, ax, y, 1, s);
+            cudaEventRecord(ev[nev++], s);
+        }
+        if (st == SPM_OK && cudaEventSynchronize(ev[nev - 1]) != cudaSuccess) st = SPM_ERR_CUDA;
+        for (int k = 1; k < nev && st == SPM_OK; ++k) {
+            float ms = 0;
+            cudaEventElapsedTime(&ms, ev[k - 1], ev[k]);
+            acc[k - 1] += ms;
+        }
+    }
+    for (int k = 0; k < 8; ++k) cudaEventDestroy(ev[k]);
+    if (st != SPM_OK) {
+        if (st == SPM_ERR_CUDA) spm_set_error("profiled apply failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return st;
+    }
+    *npasses = nev - 1;
+    for (int k = 0; k < nev - 1; ++k) pass_ms[k] = acc[k] / reps;
+    return SPM_OK;
+}
+} // namespace
+
+spm_status spm_profile_apply_impl(spm_problem_s *P, int prec, const void *x, void *y, int with_q, int reps,
+                                  float *pass_ms, int *npasses, cudaStream_t s)
+{
+    return prec == SPM_C128 ? profile_typed<double>(P, x, y, with_q, reps, pass_ms, npasses, s)
+                            : profile_typed<float>(P, x, y, with_q, reps, pass_ms, npasses, s);
 }
 
 spm_status spm_apply_A_impl(spm_problem_s *P, int prec, const void *x, void *y, int nrhs, cudaStream_t s)

@@ -165,6 +165,8 @@ struct spm_problem_s {
 spm_status spm_apply_A_impl(spm_problem_s *P, int prec, const void *x, void *y, int nrhs, cudaStream_t s);
 spm_status spm_apply_Q_impl(spm_problem_s *P, int prec, const void *v, void *y, int nrhs, cudaStream_t s);
 spm_status spm_apply_plan_impl(int prec, int L, int *get, const int *set);
+spm_status spm_profile_apply_impl(spm_problem_s *P, int prec, const void *x, void *y, int with_q, int reps,
+                                  float *pass_ms, int *npasses, cudaStream_t s);
 spm_status spm_save_plans_impl(const char *path);
 spm_status spm_load_plans_impl(const char *path, int *loaded);
 spm_status spm_wait_selftest_impl(spm_problem_s *P);

@@ -16,7 +16,8 @@
 // (T = I except in the columns p_j of its pivot rows, which the panel's storage
 // holds), Y <- T Y is  tmp = Y[P, :];  Y[P, :] = 0;  Y += panel * tmp  (a GEMM).
 // Static pivoting: a pivot below floor = tau * max |a_ij| (of the matrix before
-// elimination) is raised to the floor, phase kept, and counted.
+// elimination, computed on the device) is raised to the floor, phase kept, and
+// counted.  Nothing of the inversion waits for the host.
 #include "common.cuh"
 
 #include <algorithm>
@@ -145,7 +146,7 @@ __device__ bool grid_barrier(const GridBar &gb, unsigned nblocks)
             long it = 0;
             while (*(volatile unsigned *)gb.gen == g) {
                 if (++it > GJ_SPIN) { ok = 0; atomicExch(gb.err, 4); break; }
-                __nanosleep(64);
+                if (it > 4096) __nanosleep(64); // short waits poll without sleeping
             }
         }
         __threadfence();
@@ -156,7 +157,8 @@ __device__ bool grid_barrier(const GridBar &gb, unsigned nblocks)
 }
 
 // ------------------------------------------------------------ GJ panel
-constexpr int GJ_NB = 32, GJ_THREADS = 256;
+constexpr int GJ_NB = 32, GJ_THREADS = 512;
+static_assert(GJ_NB == 32, "the row operations map one panel column to each lane");
 
 struct GjScratch {
     double *cval; // [2][G] best |a_ij| of each block (-1: no candidate)
@@ -171,14 +173,16 @@ struct GjScratch {
 // rows [r0, r0 + nr) of the panel in shared memory.
 template <typename C>
 __global__ void __launch_bounds__(GJ_THREADS) k_gj_panel(C *S, long lds, int m, int k, int kb, int rows_per_block,
-                                                        double floor_abs, GjScratch sc, GridBar gb)
+                                                        double tau, const unsigned long long *amax, GjScratch sc,
+                                                        GridBar gb)
 {
+    const double floor_abs = tau * __longlong_as_double((long long)__ldcg(amax));
     using R = decltype(C{}.x);
     extern __shared__ unsigned char smem_raw[];
     C *sp = reinterpret_cast<C *>(smem_raw);                    // [rows_per_block][GJ_NB]
     C *cv = sp + (long)rows_per_block * GJ_NB;                 // [rows_per_block] the column entries
     int *usedl = reinterpret_cast<int *>(cv + rows_per_block); // [rows_per_block]
-    __shared__ double rv[GJ_THREADS / 32];
+    __shared__ R rv[GJ_THREADS / 32];
     __shared__ int ri[GJ_THREADS / 32];
     __shared__ int piv_s;
     const int G = gridDim.x, blk = blockIdx.x;
@@ -191,18 +195,20 @@ __global__ void __launch_bounds__(GJ_THREADS) k_gj_panel(C *S, long lds, int m, 
     __syncthreads();
     C *prow = reinterpret_cast<C *>(sc.prow);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __shared__ C prs[GJ_NB]; // the pivot row's panel entries, scaled by 1/d (entry jj: 1/d)
     for (int jj = 0; jj < kb; ++jj) {
-        // 1. this block's best unused row for column jj
-        double best = -1.0;
+        // 1. this block's best unused row for column jj (squared magnitudes compared,
+        // in the factor's own precision)
+        R best = -1;
         int bidx = -1;
         for (int i = threadIdx.x; i < nr; i += blockDim.x) {
             if (usedl[i]) continue;
             const C a = sp[i * GJ_NB + jj];
-            const double v = sqrt((double)a.x * a.x + (double)a.y * a.y);
+            const R v = a.x * a.x + a.y * a.y;
             if (v > best || (v == best && r0 + i < bidx)) { best = v; bidx = r0 + i; }
         }
         for (int o = 16; o > 0; o >>= 1) {
-            const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const R ov = __shfl_xor_sync(0xffffffffu, best, o);
             const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
             if (ov > best || (ov == best && oi >= 0 && (bidx < 0 || oi < bidx))) { best = ov; bidx = oi; }
         }
@@ -211,41 +217,63 @@ __global__ void __launch_bounds__(GJ_THREADS) k_gj_panel(C *S, long lds, int m, 
         if (threadIdx.x == 0) {
             for (int w = 1; w < GJ_THREADS / 32; ++w)
                 if (rv[w] > best || (rv[w] == best && ri[w] >= 0 && (bidx < 0 || ri[w] < bidx))) { best = rv[w]; bidx = ri[w]; }
-            sc.cval[(jj & 1) * G + blk] = best;
-            sc.cidx[(jj & 1) * G + blk] = bidx;
-            __threadfence();
-        }
-        if (!grid_barrier(gb, G)) return;
-        // 2. the pivot row: best over the blocks; its owner publishes it
-        if (threadIdx.x == 0) {
-            double bv = -1.0;
-            int bi = -1;
-            for (int g = 0; g < G; ++g) {
-                const double v = __ldcg(&sc.cval[(jj & 1) * G + g]);
-                const int ix = __ldcg(&sc.cidx[(jj & 1) * G + g]);
-                if (ix >= 0 && (v > bv || (v == bv && ix < bi))) { bv = v; bi = ix; }
+            if (G == 1) {
+                piv_s = bidx;
+            } else {
+                sc.cval[(jj & 1) * G + blk] = (double)best;
+                sc.cidx[(jj & 1) * G + blk] = bidx;
+                __threadfence();
             }
-            piv_s = bi;
+        }
+        if (G > 1) {
+            if (!grid_barrier(gb, G)) return;
+            // 2. the pivot row: best over the blocks (warp 0 reads the candidates in parallel)
+            if (wid == 0) {
+                double bv = -1.0;
+                int bi = -1;
+                for (int g = lane; g < G; g += 32) {
+                    const double v = __ldcg(&sc.cval[(jj & 1) * G + g]);
+                    const int ix = __ldcg(&sc.cidx[(jj & 1) * G + g]);
+                    if (ix >= 0 && (v > bv || (v == bv && ix < bi))) { bv = v; bi = ix; }
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                    if (oi >= 0 && (ov > bv || (ov == bv && (bi < 0 || oi < bi)))) { bv = ov; bi = oi; }
+                }
+                if (lane == 0) piv_s = bi;
+            }
         }
         __syncthreads();
         const int p = piv_s; // always >= 0: column j has m - j > 0 unused rows
-        if (p >= r0 && p < r0 + nr) {
-            for (int cc = threadIdx.x; cc < kb; cc += blockDim.x) prow[cc] = sp[(p - r0) * GJ_NB + cc];
+        const bool own = p >= r0 && p < r0 + nr;
+        if (own) {
+            for (int cc = threadIdx.x; cc < kb; cc += blockDim.x) {
+                const C v = sp[(p - r0) * GJ_NB + cc];
+                prs[cc] = v;
+                if (G > 1) prow[cc] = v;
+            }
             if (threadIdx.x == 0) {
                 usedl[p - r0] = 1;
                 sc.used[p] = 1;
                 sc.pivrow[k + jj] = p;
             }
-            __threadfence();
+            if (G > 1) __threadfence();
         }
-        if (!grid_barrier(gb, G)) return;
-        // 3. pivot (raised to the floor if tiny) and the row operations on this block's rows
-        C d = __ldcg(&prow[jj]);
-        const double ad = sqrt((double)d.x * d.x + (double)d.y * d.y);
-        if (ad < floor_abs) {
-            const double sx = ad > 0 ? d.x / ad : 1.0, sy = ad > 0 ? d.y / ad : 0.0;
-            d.x = (R)(floor_abs * sx);
-            d.y = (R)(floor_abs * sy);
+        if (G > 1) {
+            if (!grid_barrier(gb, G)) return;
+            if (!own)
+                for (int cc = threadIdx.x; cc < kb; cc += blockDim.x) prs[cc] = __ldcg(&prow[cc]);
+        }
+        __syncthreads();
+        // 3. pivot (raised to the floor if tiny), scaled pivot row, row operations
+        C d = prs[jj];
+        const R ad2 = d.x * d.x + d.y * d.y, fl = (R)floor_abs;
+        if (ad2 < fl * fl) { // rare: the static pivot floor
+            const R ad = sqrt(ad2);
+            const R sx = ad > 0 ? d.x / ad : (R)1, sy = ad > 0 ? d.y / ad : (R)0;
+            d.x = fl * sx;
+            d.y = fl * sy;
             if (blk == 0 && threadIdx.x == 0) atomicAdd(sc.raised, 1);
         }
         C one;
@@ -254,18 +282,22 @@ __global__ void __launch_bounds__(GJ_THREADS) k_gj_panel(C *S, long lds, int m, 
         const C inv_d = cdiv_(one, d);
         for (int i = threadIdx.x; i < nr; i += blockDim.x) cv[i] = sp[i * GJ_NB + jj];
         __syncthreads();
-        for (int e = threadIdx.x; e < nr * kb; e += blockDim.x) {
-            const int i = e / kb, cc = e % kb;
-            const C pr = cc == jj ? inv_d : cmul(__ldcg(&prow[cc]), inv_d); // scaled pivot row
-            if (r0 + i == p) {
-                sp[i * GJ_NB + cc] = pr;
-            } else {
-                const C a = cc == jj ? czero<C>() : sp[i * GJ_NB + cc];
-                const C c = cv[i];
-                C r;
-                r.x = a.x - (c.x * pr.x - c.y * pr.y);
-                r.y = a.y - (c.x * pr.y + c.y * pr.x);
-                sp[i * GJ_NB + cc] = r;
+        if (threadIdx.x < kb) prs[threadIdx.x] = threadIdx.x == jj ? inv_d : cmul(prs[threadIdx.x], inv_d);
+        __syncthreads();
+        // one warp per row, lane = panel column (kb <= 32)
+        if (lane < kb) {
+            const C pr = prs[lane];
+            for (int i = wid; i < nr; i += GJ_THREADS / 32) {
+                if (r0 + i == p) {
+                    sp[i * GJ_NB + lane] = pr;
+                } else {
+                    const C a = lane == jj ? czero<C>() : sp[i * GJ_NB + lane];
+                    const C c = cv[i];
+                    C r;
+                    r.x = a.x - (c.x * pr.x - c.y * pr.y);
+                    r.y = a.y - (c.x * pr.y + c.y * pr.x);
+                    sp[i * GJ_NB + lane] = r;
+                }
             }
         }
         __syncthreads();
@@ -313,13 +345,14 @@ __global__ void k_gj_inverse_perm(const int *__restrict__ pivrow, int *q, int m)
 template <typename C>
 __global__ void k_absmax(const C *__restrict__ A, long lda, int m, unsigned long long *out)
 {
-    double mx = 0;
+    using R = decltype(C{}.x);
+    R mx = 0; // largest |a|^2, in the matrix's precision
     for (long e = (long)blockIdx.x * blockDim.x + threadIdx.x; e < (long)m * m; e += (long)gridDim.x * blockDim.x) {
         const C a = A[(e / m) * lda + e % m];
-        mx = fmax(mx, sqrt((double)a.x * a.x + (double)a.y * a.y));
+        mx = max(mx, a.x * a.x + a.y * a.y);
     }
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(mx));
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(sqrt((double)mx)));
 }
 
 inline unsigned nblk(long c, int t = 256) { return (unsigned)((c + t - 1) / t); }
@@ -354,18 +387,21 @@ spm_status spm_dense_inverse(int m, C *A, long lda, C *out, long ldo, double tau
                              DenseWork *W, cudaStream_t s)
 {
     if (m <= 0) return SPM_OK;
-    // grid of the panel kernel: blocks of about 128 rows, at most what can be
-    // co-resident (cooperative launch)
+    // grid of the panel kernel: as few blocks as hold the panel's rows in shared
+    // memory (up to 768 rows in complex64, 384 in complex128), so that fronts of
+    // up to that size need no grid barrier at all; at most one block per SM
+    // (cooperative launch: every block co-resident)
     int dev = 0, sms = 0;
     SPM_CUDA_TRY(cudaGetDevice(&dev));
     SPM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    int G = (m + 127) / 128;
-    if (G > sms) G = sms;
+    const int cap = sizeof(C) == 8 ? 768 : 384;
+    int G = (m + cap - 1) / cap;
+    if (G > sms) { spm_set_error("Gauss-Jordan: front of %d unknowns is larger than %d blocks of %d rows", m, sms, cap); return SPM_ERR_INVALID_ARG; }
     const int rows = (m + G - 1) / G;
     const size_t smem = sizeof(C) * ((size_t)rows * GJ_NB + rows) + sizeof(int) * rows + 16;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_gj_panel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_gj_panel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
         attr = true;
     }
     int per_sm = 0;
@@ -397,19 +433,14 @@ spm_status spm_dense_inverse(int m, C *A, long lda, C *out, long ldo, double tau
     SPM_CUDA_TRY(cudaMemsetAsync(sc.used, 0, sizeof(int) * (size_t)m, s));
     SPM_CUDA_TRY(cudaMemsetAsync(gb.count, 0, 128, s)); // barrier words and absmax
     k_absmax<C><<<std::min(nblk((long)m * m), 1024u), 256, 0, s>>>(A, lda, m, amax);
-    unsigned long long amax_h = 0;
-    SPM_CUDA_TRY(cudaMemcpyAsync(&amax_h, amax, sizeof amax_h, cudaMemcpyDeviceToHost, s));
-    SPM_CUDA_TRY(cudaStreamSynchronize(s));
-    double amax_d;
-    memcpy(&amax_d, &amax_h, sizeof amax_d);
-    const double floor_abs = tau * amax_d;
     for (int k = 0; k < m; k += GJ_NB) {
         const int kb = std::min(GJ_NB, m - k);
         C *Sarg = A;
         long ldsarg = lda;
         int marg = m, karg = k, kbarg = kb, rowsarg = rows;
-        double flarg = floor_abs;
-        void *args[] = {&Sarg, &ldsarg, &marg, &karg, &kbarg, &rowsarg, &flarg, &sc, &gb};
+        double tauarg = tau;
+        const unsigned long long *amaxarg = amax;
+        void *args[] = {&Sarg, &ldsarg, &marg, &karg, &kbarg, &rowsarg, &tauarg, &amaxarg, &sc, &gb};
         SPM_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_gj_panel<C>, dim3(G), dim3(GJ_THREADS), args, smem, s));
         if (m > kb) {
             const long tot = (long)kb * (m - kb);

@@ -137,7 +137,8 @@ struct Tile {
 constexpr int GT_ROWS = 256, GT_COLS = 256;
 
 // out[node] += M[node][row0:+256, col0:+256] * in[node][col0:+256, :]; GT_NB
-// right-hand sides per pass over the tile (1 for a single RHS, 4 for blocks).
+// right-hand sides per pass over the tile (1 for a single RHS; 4, 8 or 16 for
+// blocks, by block size and precision).
 // S = C: stored as is; S = __half2: binary16 pairs, column c scaled by scale[c].
 __device__ __forceinline__ float2 load_as(const float2 *p) { return *p; }
 __device__ __forceinline__ double2 load_as(const double2 *p) { return *p; }
@@ -193,7 +194,9 @@ __global__ void __launch_bounds__(GT_ROWS) k_level_gemv(const S *__restrict__ M,
                     ay[b] += g.x * xv.y + g.y * xv.x;
                 }
             }
-            for (int b = 0; b < nb; ++b) {
+#pragma unroll
+            for (int b = 0; b < GT_NB; ++b) {
+                if (b >= nb) break;
                 C *o = outb + (long)(b0 + b) * nd.rows + r;
                 atomicAdd(&o->x, ax[b]);
                 atomicAdd(&o->y, ay[b]);
@@ -457,8 +460,7 @@ static spm_status factor_typed(spm_problem_s *P, NDFactor *F, bool half_store, i
     }
     // storage
     F->half_store = half_store;
-    long fac_total = 0, piv_total = 0, scale_total = 0, max_gx = 0;
-    size_t max_f = 0, max_upd_stack = 0, stack_now = 0;
+    long fac_total = 0, piv_total = 0, scale_total = 0;
     std::vector<size_t> upd_size(NN, 0);
     for (int id = 0; id < NN; ++id) {
         Node &nd = nodes[id];
@@ -469,17 +471,75 @@ static spm_status factor_typed(spm_problem_s *P, NDFactor *F, bool half_store, i
         piv_total += o3;
         nd.scale_off = scale_total;
         scale_total += f;
-        max_gx = std::max(max_gx, f * o3 + o3 * b3);
-        max_f = std::max(max_f, (size_t)f);
         F->max_own3 = std::max(F->max_own3, (size_t)o3);
         F->max_bnd3 = std::max(F->max_bnd3, (size_t)b3);
-        // stack: children's updates are popped, this node's update pushed
-        for (int ch : {nd.left, nd.right}) if (ch >= 0) stack_now -= upd_size[ch];
         upd_size[id] = (size_t)(b3 * b3);
-        stack_now += upd_size[id];
-        max_upd_stack = std::max(max_upd_stack, stack_now);
     }
-    F->max_front_unknowns = max_f;
+    // Concurrency across fronts.  A subtree whose fronts all have a fully summed
+    // block of at most GJ_ONE_BLOCK unknowns (inverted by one block, no grid
+    // barrier) is a unit of work; the maximal such subtrees are dealt round-robin
+    // to a pool of streams, each stream factoring its subtrees in postorder with
+    // its own front, update stack and dense workspace.  A subtree root's update
+    // goes to a buffer of its own, where its parent (above the subtrees, factored
+    // afterwards on the problem's stream) finds it.
+    const size_t one_block = sizeof(R) == 4 ? 768 : 384;
+    std::vector<size_t> smax(NN, 0);
+    std::vector<int> parent(NN, -1);
+    for (int id = 0; id < NN; ++id) { // postorder: children before parents
+        const Node &nd = nodes[id];
+        smax[id] = 3 * (size_t)nd.nown;
+        for (int ch : {nd.left, nd.right})
+            if (ch >= 0) { smax[id] = std::max(smax[id], smax[ch]); parent[ch] = id; }
+    }
+    std::vector<int> group(NN, -1);     // stream slot of the node, -1: above the subtrees
+    std::vector<char> sub_root(NN, 0);
+    const int NSTREAM = 16;
+    int nsub = 0;
+    for (int id = 0; id < NN; ++id)
+        if (smax[id] <= one_block && (parent[id] < 0 || smax[parent[id]] > one_block)) {
+            sub_root[id] = 1;
+            ++nsub;
+        }
+    {   // deal the subtrees (each a contiguous postorder range ending at its root)
+        int k = 0;
+        for (int id = 0; id < NN; ++id) {
+            if (!sub_root[id]) continue;
+            int first = id;
+            while (true) { // leftmost descendant = first node of the subtree's range
+                const Node &nd = nodes[first];
+                if (nd.left >= 0) first = nd.left;
+                else if (nd.right >= 0) first = nd.right;
+                else break;
+            }
+            for (int j = first; j <= id; ++j) group[j] = k % NSTREAM;
+            ++k;
+        }
+    }
+    const int ngroups = std::min(NSTREAM, std::max(nsub, 0)) + 1; // + the problem's stream (slot ngroups - 1)
+    auto slot = [&](int id) { return group[id] < 0 ? ngroups - 1 : group[id]; };
+    // per-slot workspace sizes: front, update stack (postorder within the slot; a
+    // subtree root's update lives in its own buffer), half-storage staging
+    std::vector<size_t> g_front(ngroups, 1), g_stack(ngroups, 1), g_now(ngroups, 0), g_gx(ngroups, 1);
+    std::vector<size_t> root_upd_off(NN, 0);
+    size_t root_upd_total = 0;
+    for (int id = 0; id < NN; ++id) {
+        const Node &nd = nodes[id];
+        const size_t o3 = 3 * (size_t)nd.nown, b3 = 3 * (size_t)nd.nbnd, f = o3 + b3;
+        const int g = slot(id);
+        g_front[g] = std::max(g_front[g], f * f);
+        g_gx[g] = std::max(g_gx[g], f * o3 + o3 * b3);
+        for (int ch : {nd.left, nd.right})
+            if (ch >= 0 && !sub_root[ch]) g_now[g] -= upd_size[ch];
+        if (sub_root[id]) {
+            root_upd_off[id] = root_upd_total;
+            root_upd_total += upd_size[id];
+        } else {
+            g_now[g] += upd_size[id];
+            g_stack[g] = std::max(g_stack[g], g_now[g]);
+        }
+    }
+    F->max_front_unknowns = 0;
+    for (const Node &nd : nodes) F->max_front_unknowns = std::max(F->max_front_unknowns, (size_t)(3 * (nd.nown + nd.nbnd)));
     SPM_TRY(F->pts.ensure(sizeof(int) * pts.size()));
     SPM_TRY(F->maps.ensure(sizeof(int) * maps.size()));
     SPM_TRY(F->rels.ensure(sizeof(int) * std::max<size_t>(rels.size(), 1)));
@@ -490,77 +550,120 @@ static spm_status factor_typed(spm_problem_s *P, NDFactor *F, bool half_store, i
     SPM_TRY(F->fac.ensure((half_store ? sizeof(__half2) : sizeof(C)) * fac_total));
     F->stored_bytes = (half_store ? sizeof(__half2) : sizeof(C)) * (size_t)fac_total +
                       (half_store ? sizeof(float) * (size_t)scale_total : 0);
-    DevBuf gx; // complex64 staging of G and X before conversion (half storage)
-    if (half_store) {
-        SPM_TRY(gx.ensure(sizeof(C) * max_gx));
-        SPM_TRY(F->scales.ensure(sizeof(float) * scale_total));
-    }
-    SPM_TRY(F->front.ensure(sizeof(C) * max_f * max_f));
-    SPM_TRY(F->stack.ensure(sizeof(C) * std::max<size_t>(max_upd_stack, 1)));
+    if (half_store) SPM_TRY(F->scales.ensure(sizeof(float) * scale_total));
     SPM_TRY(F->info.ensure(sizeof(int) * 3)); // expired grid barrier, unused, raised pivots
-    if (!F->dense) F->dense = spm_dense_work_new();
     SPM_CUDA_TRY(cudaMemsetAsync(F->info.ptr, 0, sizeof(int) * 3, s));
+    // per-slot buffers and streams (slot ngroups - 1 is the problem's stream)
+    struct Slot {
+        DevBuf front, stack, gx;
+        DenseWork *dense = nullptr;
+        cudaStream_t st = nullptr;
+        cudaEvent_t done = nullptr;
+        ~Slot()
+        {
+            spm_dense_work_free(dense);
+            if (st) cudaStreamDestroy(st);
+            if (done) cudaEventDestroy(done);
+        }
+    };
+    std::vector<Slot> slots(ngroups);
+    DevBuf root_upd;
+    SPM_TRY(root_upd.ensure(sizeof(C) * std::max<size_t>(root_upd_total, 1)));
+    cudaEvent_t start_ev = nullptr;
+    SPM_CUDA_TRY(cudaEventCreateWithFlags(&start_ev, cudaEventDisableTiming));
+    SPM_CUDA_TRY(cudaEventRecord(start_ev, s)); // the streams start after the work queued so far
+    for (int g = 0; g < ngroups; ++g) {
+        Slot &sl = slots[g];
+        SPM_TRY(sl.front.ensure(sizeof(C) * g_front[g]));
+        SPM_TRY(sl.stack.ensure(sizeof(C) * g_stack[g]));
+        if (half_store) SPM_TRY(sl.gx.ensure(sizeof(C) * g_gx[g]));
+        sl.dense = spm_dense_work_new();
+        if (g == ngroups - 1) {
+            sl.st = nullptr; // use s
+        } else {
+            SPM_CUDA_TRY(cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking));
+            SPM_CUDA_TRY(cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming));
+            SPM_CUDA_TRY(cudaStreamWaitEvent(sl.st, start_ev, 0));
+        }
+    }
+    cudaEventDestroy(start_ev);
 
     const C *Sdev = reinterpret_cast<const C *>(sizeof(R) == 8 ? P->S128.ptr : P->S64.ptr);
     const int *dpts = F->pts.as<int>(), *dmaps = F->maps.as<int>(), *drels = F->rels.as<int>();
-    C *front = F->front.as<C>(), *stack = F->stack.as<C>(), *fac = F->fac.as<C>();
+    C *fac = F->fac.as<C>();
     int *dinfo = F->info.as<int>();
-    std::vector<size_t> upd_pos(NN, 0);
-    size_t top = 0;
-    for (int id = 0; id < NN; ++id) {
+    std::vector<const C *> upd_ptr(NN, nullptr); // where each node's update sits
+    std::vector<size_t> top(ngroups, 0);
+    auto factor_node = [&](int id) -> spm_status {
         Node &nd = nodes[id];
+        const int g = slot(id);
+        Slot &sl = slots[g];
+        cudaStream_t ss = sl.st ? sl.st : s;
+        C *front = sl.front.as<C>(), *stack = sl.stack.as<C>();
         const int o3 = 3 * nd.nown, b3 = 3 * nd.nbnd, f = o3 + b3;
-        k_zero<C><<<blocks((long)f * f), 256, 0, s>>>(front, (long)f * f);
+        k_zero<C><<<blocks((long)f * f), 256, 0, ss>>>(front, (long)f * f);
         int ew0 = nd.ehi[0] - nd.elo[0], ew1 = nd.ehi[1] - nd.elo[1];
-        k_front_assemble<C><<<blocks((long)nd.nown * 27), 256, 0, s>>>(front, f, Sdev, dpts + nd.own_off, nd.nown,
-                                                                        dmaps + nd.map_off, nd.elo[0], nd.elo[1],
-                                                                        nd.elo[2], ew0, ew1, n);
-        // extend-add children's updates (the right child's is on top of the stack)
+        k_front_assemble<C><<<blocks((long)nd.nown * 27), 256, 0, ss>>>(front, f, Sdev, dpts + nd.own_off, nd.nown,
+                                                                         dmaps + nd.map_off, nd.elo[0], nd.elo[1],
+                                                                         nd.elo[2], ew0, ew1, n);
+        // extend-add the children's updates
         for (int ch : {nd.left, nd.right}) {
             if (ch < 0) continue;
             Node &c = nodes[ch];
             int bc = 3 * c.nbnd;
             if (bc == 0) continue;
-            k_extend_add<C><<<blocks((long)bc * bc), 256, 0, s>>>(front, f, stack + upd_pos[ch], bc, drels + c.rel_off);
+            k_extend_add<C><<<blocks((long)bc * bc), 256, 0, ss>>>(front, f, upd_ptr[ch], bc, drels + c.rel_off);
         }
-        for (int ch : {nd.left, nd.right}) if (ch >= 0) top -= upd_size[ch];
+        for (int ch : {nd.left, nd.right})
+            if (ch >= 0 && !sub_root[ch]) top[g] -= upd_size[ch];
         SPM_CUDA_TRY(cudaGetLastError());
         // F11^{-1} by Gauss-Jordan (partial pivoting inside the own block, static
         // pivot floor), then with G = [F11^{-1}; F21 F11^{-1}] (f x o3, ld f) and
         // X = F11^{-1} F12 (o3 x b3, ld o3) stored after it:
         //   X = F11^{-1} F12,  G_bottom = F21 F11^{-1},  update = F22 - F21 X.
-        C *G = half_store ? gx.as<C>() : fac + nd.fac_off;
-        SPM_TRY(spm_dense_inverse<C>(o3, front, f, G, f, pivot_floor<R>(), dinfo + 2, dinfo, F->dense, s));
+        C *G = half_store ? sl.gx.as<C>() : fac + nd.fac_off;
+        SPM_TRY(spm_dense_inverse<C>(o3, front, f, G, f, pivot_floor<R>(), dinfo + 2, dinfo, sl.dense, ss));
         if (b3 > 0) {
             C *X = G + (long)f * o3;
-            SPM_TRY(spm_dense_gemm<C>(o3, b3, o3, 1.0, G, f, front + (long)o3 * f, f, 0.0, X, o3, s));
-            SPM_TRY(spm_dense_gemm<C>(b3, o3, o3, 1.0, front + o3, f, G, f, 0.0, G + o3, f, s));
-            SPM_TRY(spm_dense_gemm<C>(b3, b3, o3, -1.0, front + o3, f, X, o3, 1.0, front + (long)o3 * f + o3, f, s));
-            // push the update
-            upd_pos[id] = top;
-            k_copy_block<C><<<blocks((long)b3 * b3), 256, 0, s>>>(stack + top, b3, front + (long)o3 * f + o3, f, b3, b3);
-            top += upd_size[id];
+            SPM_TRY(spm_dense_gemm<C>(o3, b3, o3, 1.0, G, f, front + (long)o3 * f, f, 0.0, X, o3, ss));
+            SPM_TRY(spm_dense_gemm<C>(b3, o3, o3, 1.0, front + o3, f, G, f, 0.0, G + o3, f, ss));
+            SPM_TRY(spm_dense_gemm<C>(b3, b3, o3, -1.0, front + o3, f, X, o3, 1.0, front + (long)o3 * f + o3, f, ss));
+            // keep the update: on the slot's stack, or in the subtree root's own buffer
+            C *dst = sub_root[id] ? root_upd.as<C>() + root_upd_off[id] : stack + top[g];
+            if (!sub_root[id]) top[g] += upd_size[id];
+            k_copy_block<C><<<blocks((long)b3 * b3), 256, 0, ss>>>(dst, b3, front + (long)o3 * f + o3, f, b3, b3);
+            upd_ptr[id] = dst;
         }
         if constexpr (sizeof(R) == 4) {
             if (half_store) {
                 float *sc = F->scales.as<float>() + nd.scale_off;
                 __half2 *h = F->fac.as<__half2>() + nd.fac_off;
                 const float2 *g2 = reinterpret_cast<const float2 *>(G);
-                k_col_scales<<<o3, 256, 0, s>>>(g2, f, o3, sc);
-                k_to_half<<<blocks((long)f * o3), 256, 0, s>>>(h, g2, f, o3, sc);
+                k_col_scales<<<o3, 256, 0, ss>>>(g2, f, o3, sc);
+                k_to_half<<<blocks((long)f * o3), 256, 0, ss>>>(h, g2, f, o3, sc);
                 if (b3 > 0) {
-                    k_col_scales<<<b3, 256, 0, s>>>(g2 + (long)f * o3, o3, b3, sc + o3);
-                    k_to_half<<<blocks((long)o3 * b3), 256, 0, s>>>(h + (long)f * o3, g2 + (long)f * o3, o3, b3, sc + o3);
+                    k_col_scales<<<b3, 256, 0, ss>>>(g2 + (long)f * o3, o3, b3, sc + o3);
+                    k_to_half<<<blocks((long)o3 * b3), 256, 0, ss>>>(h + (long)f * o3, g2 + (long)f * o3, o3, b3, sc + o3);
                 }
             }
         }
         SPM_CUDA_TRY(cudaGetLastError());
+        return SPM_OK;
+    };
+    // the subtrees on the stream pool, then the nodes above them on the problem's stream
+    for (int id = 0; id < NN; ++id)
+        if (group[id] >= 0) SPM_TRY(factor_node(id));
+    for (int g = 0; g < ngroups - 1; ++g) {
+        SPM_CUDA_TRY(cudaEventRecord(slots[g].done, slots[g].st));
+        SPM_CUDA_TRY(cudaStreamWaitEvent(s, slots[g].done, 0));
     }
+    for (int id = 0; id < NN; ++id)
+        if (group[id] < 0) SPM_TRY(factor_node(id));
     int hinfo[3] = {0, 0, 0};
     SPM_CUDA_TRY(cudaMemcpyAsync(hinfo, dinfo, sizeof(int) * 3, cudaMemcpyDeviceToHost, s));
     SPM_CUDA_TRY(cudaStreamSynchronize(s));
-    F->front.release();
-    F->stack.release();
+    slots.clear();
+    root_upd.release();
     F->raised_pivots = hinfo[2];
     if (hinfo[0] != 0) {
         spm_set_error("a grid barrier of the Gauss-Jordan panel expired (code %d)", hinfo[0]);
@@ -653,16 +756,25 @@ static spm_status solve_typed(spm_problem_s *P, NDFactor *F, const void *bv, voi
     const __half2 *fac16 = F->fac.as<__half2>();
     const float *scales = F->scales.as<float>();
     const LevelNode *tn = F->lv_nodes.as<LevelNode>();
+    // right-hand sides per pass over a factor tile: the tile is read once per
+    // group, so blocks of many RHS read the factor nrhs / GT_NB times
     auto gemv = [&](int ntiles, const LevelNode *nodes, const Tile *tiles) {
         if constexpr (sizeof(R) == 4) {
             if (F->half_store) {
                 if (nrhs == 1) k_level_gemv<C, 1, __half2><<<ntiles, GT_ROWS, 0, s>>>(fac16, scales, nodes, tiles, in, out, nrhs);
-                else k_level_gemv<C, 4, __half2><<<ntiles, GT_ROWS, 0, s>>>(fac16, scales, nodes, tiles, in, out, nrhs);
+                else if (nrhs < 8) k_level_gemv<C, 4, __half2><<<ntiles, GT_ROWS, 0, s>>>(fac16, scales, nodes, tiles, in, out, nrhs);
+                else if (nrhs < 16) k_level_gemv<C, 8, __half2><<<ntiles, GT_ROWS, 0, s>>>(fac16, scales, nodes, tiles, in, out, nrhs);
+                else k_level_gemv<C, 16, __half2><<<ntiles, GT_ROWS, 0, s>>>(fac16, scales, nodes, tiles, in, out, nrhs);
+                return;
+            }
+            if (nrhs >= 16) {
+                k_level_gemv<C, 16, C><<<ntiles, GT_ROWS, 0, s>>>(fac, scales, nodes, tiles, in, out, nrhs);
                 return;
             }
         }
         if (nrhs == 1) k_level_gemv<C, 1, C><<<ntiles, GT_ROWS, 0, s>>>(fac, scales, nodes, tiles, in, out, nrhs);
-        else k_level_gemv<C, 4, C><<<ntiles, GT_ROWS, 0, s>>>(fac, scales, nodes, tiles, in, out, nrhs);
+        else if (nrhs < 8) k_level_gemv<C, 4, C><<<ntiles, GT_ROWS, 0, s>>>(fac, scales, nodes, tiles, in, out, nrhs);
+        else k_level_gemv<C, 8, C><<<ntiles, GT_ROWS, 0, s>>>(fac, scales, nodes, tiles, in, out, nrhs);
     };
     const long *tu = F->lv_units.as<long>();
     const Tile *tt = F->lv_tiles.as<Tile>();

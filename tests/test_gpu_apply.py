@@ -327,3 +327,24 @@ def test_apply_plans_persist_as_json(spm, tmp_path):
     finally:
         for (pr, L), z in saved.items():
             spm.set_apply_plan(pr, L, z)
+
+
+def test_profile_apply_times_every_pass(spm):
+    """spm_profile_apply: one time per pass (x, y, z, y, x, then Q), all positive,
+    and the profiled apply leaves the same result as spm_apply_QA."""
+    n = 16
+    P, k, m, p = make(spm, n, "bumps", seed=3)
+    rng = np.random.default_rng(5)
+    al = rng.standard_normal((27, 81, 3)) + 1j * rng.standard_normal((27, 81, 3))
+    be = rng.standard_normal((27, 108, 3)) + 1j * rng.standard_normal((27, 108, 3))
+    P.set_stencils(al, be)
+    x = to_dev(si.random_field(n, 9), torch.complex64)
+    y = torch.zeros_like(x)
+    ms = P.profile_apply(x, y, with_q=True, reps=3)
+    zv = spm.get_apply_plan(spm.SPM_C64, 2 * n)
+    assert len(ms) == (4 if zv & 8 else 6) and all(v > 0 for v in ms)
+    ref = torch.zeros_like(x)
+    P.apply_QA(x, ref)
+    torch.cuda.synchronize()
+    assert torch.equal(y, ref)
+    assert len(P.profile_apply(x, y, with_q=False, reps=2)) == (3 if zv & 8 else 5)
