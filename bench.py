@@ -71,7 +71,44 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--uneven-solve-all", action="store_true",
                     help="uneven32: also solve the n = 96 problems, one after another")
+    ap.add_argument("--uneven-n96-factor", default="c64", choices=["c64", "c64h"],
+                    help="uneven32 --uneven-solve-all: factor of the n = 96 problems (complex64 or half storage)")
+    ap.add_argument("--profile-case", default=None, choices=["qa64", "a128", "a256"],
+                    help="small fixed case for ncu captures: a few applies (Q A at n = 64 with seeded random "
+                         "stencil tables, no factor; or A at n = 128 / 256) with the z-pass plan --zplan, no timing")
+    ap.add_argument("--zplan", type=int, default=0, help="apply-plan variant for --profile-case")
+    ap.add_argument("--applies", type=int, default=3, help="applies for --profile-case")
     return ap.parse_args()
+
+
+def run_profile_case(args):
+    """A small fixed workload for ncu (a few GB on the device at most): the apply
+    of the bench's medium, one right-hand side, complex64, a fixed z-pass plan.
+    For Q A the stencil tables are seeded random numbers installed with
+    spm_set_stencils (S is assembled, not factored): Q's cost does not depend on
+    their values, and the 26 GB factor of the full bench stays out of the capture."""
+    import torch
+    import paper_1804_02297_gb300 as spm
+    name = {"qa64": "n64_bumps8", "a128": "n128_bumps32_rhs8", "a256": "n256_bumps32"}[args.profile_case]
+    wl = si.workload(name)
+    n = wl["n"]
+    P = spm.Problem(n, wl["omega"], wl["eps"], wl["grad"])
+    spm.set_apply_plan(spm.SPM_C64, 2 * n, args.zplan)
+    x = torch.from_numpy(wl["einc"][:1]).to(torch.complex64).to("cuda").contiguous()
+    y = torch.zeros_like(x)
+    if args.profile_case == "qa64":
+        rng = np.random.default_rng(1)
+        P.set_stencils(rng.standard_normal((27, 81, 3)) + 1j * rng.standard_normal((27, 81, 3)),
+                       rng.standard_normal((27, 108, 3)) + 1j * rng.standard_normal((27, 108, 3)))
+        fn = P.apply_QA
+    else:
+        fn = P.apply_A
+    for _ in range(args.applies):
+        fn(x, y)
+    torch.cuda.synchronize()
+    P.device_status()
+    print(json.dumps({"profile_case": args.profile_case, "workload": name, "zplan": args.zplan,
+                      "applies": args.applies, "device_gb": torch.cuda.max_memory_allocated() / 1e9}))
 
 
 def dist_env():
@@ -126,7 +163,7 @@ def zpass_name(spm, prec, L):
     if z < 0:
         return "not chosen"
     name = {0: "four-line", 1: "one-field prefetch", 2: "TMA-fed persistent", 3: "16 per thread",
-            4: "staged spectra"}.get(z & 7, "?")
+            4: "staged spectra", 5: "even/odd split"}.get(z & 7, "?")
     return name + (" + fused x/y plane passes" if z & 8 else "")
 
 
@@ -410,7 +447,7 @@ def run_uneven(args, torch, spm, rank, world, local):
                 Pq = spm.Problem(q["n"], q["omega"], q["eps"], q["grad"])
                 t0 = time.perf_counter()
                 try:
-                    Pq.build_stencils(spm.SPM_C64H)
+                    Pq.build_stencils(spm.SPM_C64 if args.uneven_n96_factor == "c64" else spm.SPM_C64H)
                 except spm.SpmError as err:
                     rows.append({"status": err.status, "error": str(err), "free_gb_before": free_gb})
                     Pq.close()
@@ -774,12 +811,15 @@ def run_ours(args):
         line["roofline"]["z_pass"] = {"kernel": "z-pass (" + zpass_name(spm, args.prec, L) + ")", "bound": "alu",
                                       "ms": pass_ms[iz], "algorithmic_flops": z_flops,
                                       "achieved": z_flops / (pass_ms[iz] / 1000.0) / 1e12, "peak": fpeak,
-                                      "unit": "TFLOP/s", "frac": z_flops / (pass_ms[iz] / 1000.0) / fpk}
+                                      "unit": "TFLOP/s", "frac": z_flops / (pass_ms[iz] / 1000.0) / fpk,
+                                      "traffic": recorded_traffic(args.workload, args.prec,
+                                                                  "zpass-" + zpass_name(spm, args.prec, L))}
         if args.op == "QA":
             line["roofline"]["q_gather"] = {"kernel": "k_q", "bound": "alu", "ms": pass_ms[-1],
                                             "algorithmic_flops": q_flops,
                                             "achieved": q_flops / (pass_ms[-1] / 1000.0) / 1e12, "peak": fpeak,
-                                            "unit": "TFLOP/s", "frac": q_flops / (pass_ms[-1] / 1000.0) / fpk}
+                                            "unit": "TFLOP/s", "frac": q_flops / (pass_ms[-1] / 1000.0) / fpk,
+                                            "traffic": recorded_traffic(args.workload, args.prec, "q")}
     if args.prec == "c64" and nrhs == 1:
         # the apply of A alone, hand-written passes against the cuFFT comparison apply
         a_ms = time_apply(torch, P.apply_A, x, y, 200 if n <= 64 else 20)
@@ -807,6 +847,9 @@ def run_ours(args):
 
 def main():
     args = parse()
+    if args.profile_case:
+        run_profile_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -224,6 +224,9 @@ spm_status spm_solve_S(spm_problem prob, spm_prec prec, const void *b_dev, void 
  *      (L = 128, 256, 512),
  *   4  as 1, with the tile's kernel spectra and the twiddle table also staged
  *      in shared memory by cp.async (L >= 32),
+ *   5  each length-2n transform split into two length-n transforms of the
+ *      even and odd frequencies, which share their exchanges (L = 64, 128,
+ *      256),
  *  -1  not chosen yet: the next apply of that length times the candidates on
  *      its own data (outside stream capture) and keeps the fastest.
  * Plus 8 (L = 64, 128 only): the x- and y-passes of each z-plane run fused in
@@ -246,7 +249,7 @@ spm_status spm_profile_apply(spm_problem prob, spm_prec prec, const void *x_dev,
 
 /* The autotuner's choices persisted as JSON: {"device": name, "plans": [{"prec":
  * "c64" | "c128", "L": length, "variant": v, "ms": [per-apply ms of variants
- * 0..4 when they were timed, else 0], "fused_xy_ms": ms of the best variant with
+ * 0..5 when they were timed, else 0], "fused_xy_ms": ms of the best variant with
  * fused x and y passes, else 0}, ...]} for every (precision, length) whose
  * variant is set.  spm_load_apply_plans installs the entries of a file written
  * on a device of the same name (SPM_ERR_INVALID_ARG for another device or an

@@ -32,7 +32,7 @@ EXPORTS = [
 ]
 
 
-ZPASS_FOUR, ZPASS_ONE, ZPASS_TMA, ZPASS_E16, ZPASS_STAGED = 0, 1, 2, 3, 4
+ZPASS_FOUR, ZPASS_ONE, ZPASS_TMA, ZPASS_E16, ZPASS_STAGED, ZPASS_SPLIT = 0, 1, 2, 3, 4, 5
 PLAN_FUSED_XY = 8  # add to a z-pass variant: x and y passes fused per z-plane (L = 64, 128)
 
 

@@ -80,7 +80,7 @@ template <typename R, int L> struct tx_of {
     static constexpr int v = w < L ? w : L; // never wider than a row of L elements
 };
 
-constexpr int ZPROD_FOUR = 0, ZPROD_ONE = 1, ZPROD_TMA = 2, ZPROD_E16 = 3, ZPROD_STAGED = 4; // z-pass kernel choices
+constexpr int ZPROD_FOUR = 0, ZPROD_ONE = 1, ZPROD_TMA = 2, ZPROD_E16 = 3, ZPROD_STAGED = 4, ZPROD_SPLIT = 5; // z-pass kernels
 constexpr int ZPLAN_FUSED_XY = 8; // plan bit: x and y passes fused per z-plane (L = 64, 128)
 
 template <int L> __device__ __forceinline__ int xpad(int pos) { return pos + (pos >> 3); }
@@ -439,6 +439,91 @@ __global__ void __launch_bounds__(zst<R, L>::THREADS) k2_zstaged(typename cplx_o
         line_fft<1, L, false>(v, t, buf, sync, stw);
 #pragma unroll
         for (int q = 0; q < H; ++q) base[d * fs + (long)(t + T * q) * L2] = v[q];
+    }
+}
+
+// zprod, split into even and odd frequencies (L = 64, 128, 256): with
+// H = L/2 = n and x[z] = 0 for z >= H,
+//   X[2k]     = DFT_H(x)[k],   X[2k + 1] = DFT_H(x . w_L^z)[k],
+// and the inverse restricted to z < H is
+//   y[z] = IDFT_H(Y_even)[z] + conj(w_L^z) IDFT_H(Y_odd)[z],
+// so every length-L transform of the z-pass becomes two length-H transforms
+// that share their exchanges (fftr::fft_lines with K = 2), and the radix-2
+// stage of L = 128 disappears.  256 threads: TX = 256 / (H/8) columns.
+template <typename R, int L> struct zsp {
+    using C = typename cplx_of<R>::type;
+    static constexpr int H = L / 2, T = H / 8, TX = 256 / T;
+    // exchange [2][H][TX], transformed p.E [16][256] (each thread its own), tables H + L
+    static constexpr size_t smem = sizeof(C) * ((size_t)2 * H * TX + 16 * 256 + H + L);
+    static_assert(L == 64 || L == 128 || L == 256, "split z-pass lengths");
+};
+
+template <typename R, int L>
+__global__ void __launch_bounds__(256, 2) k2_zsplit(typename cplx_of<R>::type *W2,
+                                                 const typename cplx_of<R>::type *__restrict__ spec,
+                                                 const typename cplx_of<R>::type *__restrict__ tw)
+{
+    pdl_wait_and_trigger();
+    using C = typename cplx_of<R>::type;
+    constexpr int H = zsp<R, L>::H, T = zsp<R, L>::T, TX = zsp<R, L>::TX, n = H, n1 = n + 1;
+    constexpr long L2 = (long)L * L, oct = (long)n1 * n1 * n1, fs = (long)n * L * L;
+    extern __shared__ unsigned char smem_raw[];
+    C *xch = reinterpret_cast<C *>(smem_raw); // [2 lines][H][TX]
+    C *w4s = xch + 2 * H * TX;               // transformed p.E: [16][256], thread-private columns
+    C *stw = w4s + 16 * 256;                 // length-H twiddles: w_H^j = w_L^(2j)
+    C *stl = stw + H;                        // length-L twiddles w_L^j
+    const int c = threadIdx.x % TX, t = threadIdx.x / TX;
+    const long col = (long)blockIdx.x * TX + c;
+    const int b = blockIdx.y;
+    C *base = W2 + (long)b * 4 * fs + col;
+    const int eta = (int)(col / L), xi = (int)(col % L);
+    const int a1 = xi <= n ? xi : L - xi, a2 = eta <= n ? eta : L - eta;
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        const C w = tw[i];
+        stl[i] = w;
+        if ((i & 1) == 0) stw[i >> 1] = w;
+    }
+    __syncthreads();
+    auto buf = [&](int k, int pos) -> C & { return xch[(k * H + pos) * TX + c]; };
+    auto sync = [&]() { __syncthreads(); };
+    // forward: field f -> (even, odd) halves of its spectrum at k = t + T m
+    auto forward = [&](int f, C (&v)[2][8]) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const C xz = base[f * fs + (long)(t + T * q) * L2];
+            v[0][q] = xz;
+            v[1][q] = cmul(xz, stl[t + T * q]);
+        }
+        fftr::fft_lines<-1, H, false, 2>(v, t, buf, sync, stw);
+    };
+    {
+        C w4[2][8];
+        forward(3, w4);
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int q = 0; q < 8; ++q) w4s[(h * 8 + q) * 256 + threadIdx.x] = w4[h][q];
+    }
+#pragma unroll 1
+    for (int d = 0; d < 3; ++d) {
+        C v[2][8];
+        forward(d, v);
+        const int fr_fixed = d == 0 ? xi : eta;
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int zeta = 2 * (t + T * q) + h;
+                const int a3 = zeta <= n ? zeta : L - zeta;
+                const long o = ((long)a3 * n1 + a2) * n1 + a1;
+                C K0 = spec[o], Kd = spec[(1 + d) * oct + o];
+                const int fr = d == 2 ? zeta : fr_fixed;
+                if (fr > n) { Kd.x = -Kd.x; Kd.y = -Kd.y; }
+                v[h][q] = cfma(K0, v[h][q], cmul(Kd, w4s[(h * 8 + q) * 256 + threadIdx.x]));
+            }
+        fftr::fft_lines<1, H, false, 2>(v, t, buf, sync, stw);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) base[d * fs + (long)(t + T * q) * L2] = v[0][q] + cmulc(v[1][q], stl[t + T * q]);
     }
 }
 
@@ -1083,6 +1168,18 @@ spm_status apply_chunk_v2(const typename cplx_of<R>::type *xb, typename cplx_of<
             done = true;
         }
     }
+    if constexpr (L == 64 || L == 128 || L == 256) {
+        if (!done && zvar == ZPROD_SPLIT) {
+            static bool asp = false;
+            if (!asp) {
+                allow_smem(k2_zsplit<R, L>, zsp<R, L>::smem);
+                asp = true;
+            }
+            launch_pdl(k2_zsplit<R, L>, dim3((unsigned)(L2 / zsp<R, L>::TX), nb), dim3(256), zsp<R, L>::smem, s, W2,
+                       spec, tw);
+            done = true;
+        }
+    }
     if constexpr (line_elems(L) == 8) {
         if (!done && zvar == ZPROD_FOUR) {
             launch_pdl(k2_zprod4<R, L>, dim3((unsigned)(L2 / TX), nb), dim3(THR), sm_zprod4, s, W2, spec, tw);
@@ -1144,7 +1241,7 @@ spm_status run_chunk(int L, const typename cplx_of<R>::type *xb, typename cplx_o
 std::atomic<int> g_zplan[2][10];
 std::atomic<int> g_zplan_init(0);
 // per-apply ms of each candidate when the plan timed them (0: not timed)
-float g_ztime[2][10][5];
+float g_ztime[2][10][6];
 float g_ztime_fused[2][10]; // the chosen z-pass with fused x and y passes (0: not timed)
 std::mutex g_ztime_mu;
 
@@ -1179,12 +1276,13 @@ spm_status choose_zplan(int L, const typename cplx_of<R>::type *xb, typename cpl
     int z = zplan_get(pi, L);
     if (z >= 0) { *zvar = z; return SPM_OK; }
     const int fallback = line_elems(L) == 8 ? ZPROD_FOUR : ZPROD_ONE;
-    int cands[5], nc = 0;
+    int cands[6], nc = 0;
     if (line_elems(L) == 8) cands[nc++] = ZPROD_FOUR;
     if (line_elems(L) != 8 || L >= 32) cands[nc++] = ZPROD_ONE;
     if (L >= 32) cands[nc++] = ZPROD_TMA;
     if (L == 128 || L == 256 || L == 512) cands[nc++] = ZPROD_E16;
     if (L >= 32) cands[nc++] = ZPROD_STAGED;
+    if (L == 64 || L == 128 || L == 256) cands[nc++] = ZPROD_SPLIT;
     if (nc == 1) { g_zplan[pi][len_index(L)].store(cands[0]); *zvar = cands[0]; return SPM_OK; }
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     SPM_CUDA_TRY(cudaStreamIsCapturing(s, &cap));
@@ -1196,7 +1294,7 @@ spm_status choose_zplan(int L, const typename cplx_of<R>::type *xb, typename cpl
     int best_z = fallback;
     spm_status st = SPM_OK;
     const int reps = L >= 512 ? 3 : (L >= 256 ? 5 : 10);
-    float times[5] = {0, 0, 0, 0, 0};
+    float times[6] = {0, 0, 0, 0, 0, 0};
     for (int ci = 0; ci < nc; ++ci) {
         const int cand = cands[ci];
         st = run_chunk<R>(L, xb, yb, m, p, spec, tw, W1, W2, nb, cand, err, s); // warm-up
@@ -1231,7 +1329,7 @@ spm_status choose_zplan(int L, const typename cplx_of<R>::type *xb, typename cpl
     }
     if (st == SPM_OK) {
         std::lock_guard<std::mutex> lock(g_ztime_mu);
-        for (int v = 0; v < 5; ++v) g_ztime[pi][len_index(L)][v] = times[v];
+        for (int v = 0; v < 6; ++v) g_ztime[pi][len_index(L)][v] = times[v];
         g_ztime_fused[pi][len_index(L)] = fused_ms;
     }
     cudaEventDestroy(e0);
@@ -1609,7 +1707,8 @@ static int zplan_supported(int L)
 {
     const bool e8 = !(L == 96 || L == 192);
     return (e8 ? 1 << ZPROD_FOUR : 0) | ((!e8 || L >= 32) ? 1 << ZPROD_ONE : 0) | (L >= 32 ? 1 << ZPROD_TMA : 0) |
-           ((L == 128 || L == 256 || L == 512) ? 1 << ZPROD_E16 : 0) | (L >= 32 ? 1 << ZPROD_STAGED : 0);
+           ((L == 128 || L == 256 || L == 512) ? 1 << ZPROD_E16 : 0) | (L >= 32 ? 1 << ZPROD_STAGED : 0) |
+           ((L == 64 || L == 128 || L == 256) ? 1 << ZPROD_SPLIT : 0);
 }
 
 spm_status spm_wait_selftest_impl(spm_problem_s *P)
@@ -1626,7 +1725,7 @@ spm_status spm_apply_plan_impl(int prec, int L, int *get, const int *set)
     if (set) {
         const int zpart = *set & (ZPLAN_FUSED_XY - 1);
         const bool fz = *set >= 0 && (*set & ZPLAN_FUSED_XY) != 0;
-        if (*set != -1 && (*set < 0 || *set > (ZPLAN_FUSED_XY | 4) || !(zplan_supported(L) & (1 << zpart)) ||
+        if (*set != -1 && (*set < 0 || *set > (ZPLAN_FUSED_XY | 5) || !(zplan_supported(L) & (1 << zpart)) ||
                            (fz && L != 64 && L != 128))) {
             spm_set_error("z-pass variant %d is not available for FFT length %d", *set, L);
             return SPM_ERR_INVALID_ARG;
@@ -1659,10 +1758,10 @@ spm_status spm_save_plans_impl(const char *path)
             const int z = zplan_get(pi, L);
             if (z < 0) continue;
             char buf[256];
-            float t[5];
+            float t[6];
             {
                 std::lock_guard<std::mutex> lock(g_ztime_mu);
-                for (int v = 0; v < 5; ++v) t[v] = g_ztime[pi][li][v];
+                for (int v = 0; v < 6; ++v) t[v] = g_ztime[pi][li][v];
             }
             float tf;
             {
@@ -1670,9 +1769,9 @@ spm_status spm_save_plans_impl(const char *path)
                 tf = g_ztime_fused[pi][li];
             }
             snprintf(buf, sizeof buf,
-                     "%s\n    {\"prec\": \"%s\", \"L\": %d, \"variant\": %d, \"ms\": [%.6g, %.6g, %.6g, %.6g, %.6g], "
+                     "%s\n    {\"prec\": \"%s\", \"L\": %d, \"variant\": %d, \"ms\": [%.6g, %.6g, %.6g, %.6g, %.6g, %.6g], "
                      "\"fused_xy_ms\": %.6g}",
-                     first ? "" : ",", pi == 0 ? "c128" : "c64", L, z, t[0], t[1], t[2], t[3], t[4], tf);
+                     first ? "" : ",", pi == 0 ? "c128" : "c64", L, z, t[0], t[1], t[2], t[3], t[4], t[5], tf);
             out += buf;
             first = false;
         }

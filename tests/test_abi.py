@@ -62,7 +62,7 @@ def test_host_side_settings_without_gpu(spm):
     lib = spm.lib
     saved = spm.get_apply_plan(spm.SPM_C64, 128)
     try:
-        for z in (spm.ZPASS_FOUR, spm.ZPASS_ONE, spm.ZPASS_TMA, spm.ZPASS_E16, spm.ZPASS_STAGED, -1):
+        for z in (spm.ZPASS_FOUR, spm.ZPASS_ONE, spm.ZPASS_TMA, spm.ZPASS_E16, spm.ZPASS_STAGED, spm.ZPASS_SPLIT, -1):
             spm.set_apply_plan(spm.SPM_C64, 128, z)
             assert spm.get_apply_plan(spm.SPM_C64, 128) == z
     finally:
@@ -71,7 +71,7 @@ def test_host_side_settings_without_gpu(spm):
     assert lib.spm_set_apply_plan(spm.SPM_C64, 16, spm.ZPASS_TMA) == spm.SPM_ERR_INVALID_ARG  # too short for TMA
     assert lib.spm_set_apply_plan(spm.SPM_C64, 100, spm.ZPASS_ONE) == spm.SPM_ERR_INVALID_ARG  # no such length
     assert lib.spm_set_apply_plan(spm.SPM_MIXED, 128, spm.ZPASS_ONE) == spm.SPM_ERR_INVALID_ARG
-    assert lib.spm_set_apply_plan(spm.SPM_C64, 128, 5) == spm.SPM_ERR_INVALID_ARG  # no such variant
+    assert lib.spm_set_apply_plan(spm.SPM_C64, 128, 6) == spm.SPM_ERR_INVALID_ARG  # no such variant
     rep = spm.FactorReport()
     assert lib.spm_factor_info(None, spm.SPM_C64, ctypes.byref(rep)) == spm.SPM_ERR_INVALID_ARG
     assert lib.spm_device_status(None) == spm.SPM_ERR_INVALID_ARG

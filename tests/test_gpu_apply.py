@@ -218,6 +218,8 @@ def _zpass_variants(spm, L):
     v = [spm.ZPASS_FOUR, spm.ZPASS_ONE, spm.ZPASS_TMA, spm.ZPASS_STAGED] if L >= 32 else [spm.ZPASS_FOUR]
     if L in (128, 256, 512):
         v.append(spm.ZPASS_E16)
+    if L in (64, 128, 256):
+        v.append(spm.ZPASS_SPLIT)
     if L in (64, 128):  # the same z-pass kernels with the x and y passes fused per plane
         v += [z | spm.PLAN_FUSED_XY for z in list(v)]
     return v
