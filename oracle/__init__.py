@@ -1,6 +1,7 @@
 """FP64 CPU oracle (TEST INFRASTRUCTURE ONLY).
 
-Plain C (``spmref.c``) behind ctypes, plus the radial closed form in ``radial.py``.
+Plain C (``spmref.c``) behind ctypes, plus the radial closed form in ``radial.py``
+and the 2-D variant in numpy/scipy (``twod.py``).
 Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  It shares no code with the CUDA library.
 

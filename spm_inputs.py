@@ -273,3 +273,120 @@ def uneven_batch(count: int = 32, sizes=(32, 48, 64, 96), base_seed: int = 100):
         einc = plane_wave(n, k, (0, 0, 1), (1, 0, 0))
         out.append(dict(n=n, omega=k, eps=eps, grad=grad, einc=einc))
     return out
+
+
+# ------------------------------------------------------------- 2-D inputs ----
+# The 2-D variant (Sections 2 and 4): Omega = (0,1)^2, n points per dimension,
+# h = 1/(n+1), arrays [i2][i1], vector fields [d][i2][i1] with two components.
+# Media stand in for the three 2-D examples of Section 4, which are given only in
+# words (a converging Gaussian lens, a square obstacle with smooth boundary, a
+# random perturbation of that obstacle).
+
+def wavenumber_for_grid_2d(n: int) -> float:
+    """k = 2 pi (n+1)/6: six points per background wavelength, as in Section 4
+    (n = 119 gives k/2pi = 20, the first row of Tables 1-3)."""
+    return 2.0 * math.pi * (n + 1) / 6.0
+
+
+def _window_1d(t, lo, hi, delta):
+    """b(t) = S((t-lo)/delta) S((hi-t)/delta) and b'(t): 1 on [lo+delta, hi-delta], 0 outside (lo, hi)."""
+    u, v = (t - lo) / delta, (hi - t) / delta
+    b = _step(u) * _step(v)
+    db = _dstep(u) * _step(v) / delta - _step(u) * _dstep(v) / delta
+    return b, db
+
+
+def medium2_lens(n: int, amplitude: float = 0.5, width: float = 0.12):
+    """Converging Gaussian lens eps = 1 + a exp(-|x-c|^2/(2 w^2)) T(x), c = (1/2,1/2),
+    T(x) = s(x1) s(x2) the taper; returns (eps (n,n), grad_eps (2,n,n))."""
+    x, _ = grid_coords(n)
+    X2, X1 = np.meshgrid(x, x, indexing="ij")
+    e = amplitude * np.exp(-((X1 - 0.5) ** 2 + (X2 - 0.5) ** 2) / (2.0 * width * width))
+    s1, ds1 = taper_1d(X1)
+    s2, ds2 = taper_1d(X2)
+    T = s1 * s2
+    g1 = -e * (X1 - 0.5) / (width * width)
+    g2 = -e * (X2 - 0.5) / (width * width)
+    eps = 1.0 + T * e
+    grad = np.stack([ds1 * s2 * e + T * g1, s1 * ds2 * e + T * g2])
+    return eps.astype(np.complex128), grad.astype(np.complex128)
+
+
+def _square_profile(n, lo=0.3, hi=0.7, delta=0.06):
+    x, _ = grid_coords(n)
+    X2, X1 = np.meshgrid(x, x, indexing="ij")
+    b1, db1 = _window_1d(X1, lo, hi, delta)
+    b2, db2 = _window_1d(X2, lo, hi, delta)
+    return X1, X2, b1 * b2, db1 * b2, b1 * db2
+
+
+def medium2_square(n: int, amplitude: float = 0.4):
+    """Square obstacle with smooth boundary: eps = 1 + a b(x1) b(x2), b the smooth
+    window that is 1 on [0.36, 0.64] and 0 outside (0.3, 0.7)."""
+    _, _, B, dB1, dB2 = _square_profile(n)
+    eps = 1.0 + amplitude * B
+    grad = np.stack([amplitude * dB1, amplitude * dB2])
+    return eps.astype(np.complex128), grad.astype(np.complex128)
+
+
+def medium2_random(n: int, seed: int = 7, amplitude: float = 0.4, count: int = 24):
+    """Random perturbation of the square obstacle: eps = 1 + b(x1) b(x2) (a + rho(x)),
+    rho = sum of ``count`` Gaussian bumps with amplitude U[-0.15,0.15], width
+    U[0.02,0.05], centre U[0.3,0.7]^2 (splitmix64, drawn in that order)."""
+    X1, X2, B, dB1, dB2 = _square_profile(n)
+    rng = SplitMix64(seed)
+    rho = np.zeros_like(X1)
+    dr1 = np.zeros_like(X1)
+    dr2 = np.zeros_like(X1)
+    for _ in range(count):
+        a = -0.15 + 0.3 * rng.uniform()
+        w = 0.02 + 0.03 * rng.uniform()
+        c1 = 0.3 + 0.4 * rng.uniform()
+        c2 = 0.3 + 0.4 * rng.uniform()
+        e = a * np.exp(-((X1 - c1) ** 2 + (X2 - c2) ** 2) / (2.0 * w * w))
+        rho += e
+        dr1 += -e * (X1 - c1) / (w * w)
+        dr2 += -e * (X2 - c2) / (w * w)
+    q = amplitude + rho
+    eps = 1.0 + B * q
+    grad = np.stack([dB1 * q + B * dr1, dB2 * q + B * dr2])
+    return eps.astype(np.complex128), grad.astype(np.complex128)
+
+
+def plane_wave_2d(n: int, k: float):
+    """The incident field of Section 4 (2-D): E^i = (0, e^{i k x1}), shape (2, n, n)."""
+    x, _ = grid_coords(n)
+    X2, X1 = np.meshgrid(x, x, indexing="ij")
+    return np.stack([np.zeros_like(X1, dtype=np.complex128), np.exp(1j * k * X1)])
+
+
+def random_field_2d(n: int, seed: int, nrhs: int | None = None):
+    """Standard complex normal test vector of shape (2,n,n) or (nrhs,2,n,n)."""
+    rng = np.random.default_rng(seed)
+    shape = (2, n, n) if nrhs is None else (nrhs, 2, n, n)
+    return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)).astype(np.complex128)
+
+
+def random_medium_2d(n: int, seed: int, amplitude: float = 0.3):
+    """Rough random complex eps with a random gradient (algebraic tests only)."""
+    rng = np.random.default_rng(seed)
+    eps = 1.0 + amplitude * (rng.uniform(0, 1, (n, n)) + 0.2j * rng.uniform(0, 1, (n, n)))
+    grad = amplitude * (rng.standard_normal((2, n, n)) + 1j * rng.standard_normal((2, n, n)))
+    return eps.astype(np.complex128), grad.astype(np.complex128)
+
+
+def workload_2d(name: str):
+    """'<medium>2d_n<n>' with medium lens | square | random, e.g. 'lens2d_n119':
+    returns dict(n, omega, eps, grad, einc) with einc of shape (1, 2, n, n)."""
+    med, _, size = name.partition("2d_n")
+    n = int(size)
+    k = wavenumber_for_grid_2d(n)
+    if med == "lens":
+        eps, grad = medium2_lens(n)
+    elif med == "square":
+        eps, grad = medium2_square(n)
+    elif med == "random":
+        eps, grad = medium2_random(n)
+    else:
+        raise KeyError(name)
+    return dict(n=n, omega=k, eps=eps, grad=grad, einc=plane_wave_2d(n, k)[None])

@@ -16,11 +16,12 @@ def pytest_configure(config):
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
-def read_paper_iteration_counts():
-    """Rows (medium, k/2pi, n, N_iter) of tests/golden/paper_iteration_counts.txt:
-    the preconditioned GMRES(20) iteration counts of the paper's 3-D Tables 4-6."""
+def read_paper_iteration_counts(fname="paper_iteration_counts.txt"):
+    """Rows (medium, k/2pi, n, N_iter) of a golden file: the preconditioned GMRES(20)
+    iteration counts of the paper's 3-D Tables 4-6 (paper_iteration_counts.txt) or
+    2-D Tables 1-3 (paper_iteration_counts_2d.txt)."""
     rows = []
-    with open(os.path.join(GOLDEN, "paper_iteration_counts.txt")) as f:
+    with open(os.path.join(GOLDEN, fname)) as f:
         for line in f:
             line = line.split("#", 1)[0].strip()
             if not line:
@@ -33,3 +34,8 @@ def read_paper_iteration_counts():
 @pytest.fixture(scope="session")
 def paper_iteration_counts():
     return read_paper_iteration_counts()
+
+
+@pytest.fixture(scope="session")
+def paper_iteration_counts_2d():
+    return read_paper_iteration_counts("paper_iteration_counts_2d.txt")
