@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--solve", default="both", choices=["none", "mixed", "both"])
     ap.add_argument("--no-block-solve", action="store_true",
                     help="skip the 64-RHS block solve (config 3) in the default n = 64 run")
+    ap.add_argument("--no-2d", action="store_true", help="skip the 2-D variant's apply and solve measurements")
     ap.add_argument("--no-n256", action="store_true",
                     help="skip the n = 256 apply sub-measurement of the default run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -625,6 +626,69 @@ def measure_n256(spm, torch, apk, hbm_peak, hbm_kind, steps=12, warmup=3):
     return out
 
 
+# Section 4, Tables 1-3 (2-D, MATLAB on four Xeon E7-4830 v3): per k/2pi (n =
+# 119, 239, 479, 959) the set-up, apply and solve seconds and iteration counts
+# of the Gaussian lens (Table 1), context for the 2-D numbers (another machine).
+PAPER_2D_LENS = {119: (1.25, 5.58e-2, 6, 9.13e-1), 239: (5.52, 3.27e-1, 6, 2.51), 479: (21.7, 1.40, 6, 8.93),
+                 959: (98.7, 5.03, 6, 41.3)}
+
+
+def measure_2d(spm, torch, apk, hbm_peak, hbm_kind, sizes=(119, 239, 479, 959), steps=20):
+    """The 2-D variant (include/spm2d.h) at the four sizes of the paper's 2-D
+    tables (N = 2 n^2, six points per wavelength): device time of the apply of A
+    (one right-hand side, complex64 and complex128, L2 flushed between applies)
+    with its algorithmic bytes and flops against the measured peaks; then the
+    Gaussian-lens solve to 1e-6 (stencils fitted on the device, complex64 factor,
+    mixed-precision GMRES(20)), set-up and solve wall times and iterations."""
+    out = {"sizes": list(sizes), "apply": [], "solve": [],
+           "paper_table1_lens_s": {str(n): {"setup": v[0], "apply": v[1], "iterations": v[2], "solve": v[3]}
+                                   for n, v in PAPER_2D_LENS.items()}}
+    for n in sizes:
+        wl = si.workload_2d(f"lens2d_n{n}")
+        t0 = time.perf_counter()
+        P = spm.Problem2D(n, wl["omega"], wl["eps"], wl["grad"])
+        torch.cuda.synchronize()
+        t_create = time.perf_counter() - t0
+        L = P.info()[1]
+        N, H = n * n, L // 2 + 1
+        flops = 5.0 * L * np.log2(L) * (3 * n + 5 * L + 2 * n) + 32.0 * L * L
+        for prec, dt, el in (("c64", torch.complex64, 8), ("c128", torch.complex128, 16)):
+            x = torch.from_numpy(wl["einc"]).to(dt).to("cuda").contiguous()
+            y = torch.zeros_like(x)
+            ms = time_apply(torch, P.apply_A, x, y, steps)
+            alg = el * (7 * N + 3 * H * H)
+            fpk = apk["fp32"] if prec == "c64" else apk["fp64"]
+            out["apply"].append({"n": n, "L": L, "dtype": prec, "ms": ms, "algorithmic_bytes": alg,
+                                 "hbm_frac": alg / (ms / 1000.0) / 1e9 / hbm_peak, "algorithmic_flops": flops,
+                                 "alu_frac": flops / (ms / 1000.0) / 1e12 / fpk,
+                                 "alu_peak": "fp32" if prec == "c64" else "fp64"})
+            del x, y
+        t1 = time.perf_counter()
+        P.build_stencils(spm.SPM_C64)
+        torch.cuda.synchronize()
+        t_setup = time.perf_counter() - t1
+        e = torch.from_numpy(wl["einc"]).to("cuda")
+        g = torch.zeros_like(e)
+        P.rhs_from_incident(e, g)
+        x = torch.zeros_like(g)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        info, st = P.solve(g, x, prec=spm.SPM_MIXED, tol=1e-6, maxit=200, restart=20, check=False)
+        torch.cuda.synchronize()
+        out["solve"].append({"n": n, "unknowns": 2 * N, "k_over_2pi": wl["omega"] / (2 * np.pi),
+                             "create_s": t_create, "stencils_and_factor_s": t_setup,
+                             "solve_s": time.perf_counter() - t2, "iterations": info.iterations,
+                             "true_relres": info.true_relres, "status": st,
+                             "factor_probe": P.factor_info(spm.SPM_C64)[3]})
+        P.close()
+        del P, e, g, x
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    out["hbm_peak_gbs"] = hbm_peak
+    out["hbm_peak_source"] = hbm_kind
+    return out
+
+
 def measure_block_solve(spm, torch, P, args):
     """Config 3: the 64 incident plane waves (32 Fibonacci directions x 2
     polarisations) of the n = 64 medium as one block right-hand side, solved to a
@@ -837,6 +901,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
         line["apply_n256"] = measure_n256(spm, torch, apk, peak, peak_kind)
+    if args.workload == "n64_bumps8" and not args.no_2d:
+        line["twod"] = measure_2d(spm, torch, apk, peak, peak_kind)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds, args.op, single_thread_seconds=5.0)
     if rank == 0:

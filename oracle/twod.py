@@ -146,6 +146,26 @@ def apply_direct(n, k, m, p, x, quad=QUAD_ORDER4):
     return y.reshape(2, n, n)
 
 
+def apply_direct_points(n, k, m, p, x, idx, quad=QUAD_ORDER4, E=None):
+    """(A x) at the linear point indices idx (i2 * n + i1) by the direct sum of
+    Eq. discrete (2-D): shape (len(idx), 2).  E: the entry table, if already built."""
+    x = np.asarray(x, np.complex128)
+    if E is None:
+        E = kernel_entries(n, k, quad)
+    w = _weights(m, p, x).reshape(3, -1)
+    j = np.arange(n * n)
+    J1, J2 = j % n, j // n
+    out = np.zeros((len(idx), 2), np.complex128)
+    k2 = k * k
+    for r, i in enumerate(idx):
+        t1 = i % n - J1 + n - 1
+        t2 = i // n - J2 + n - 1
+        g, g1, g2 = E[0, t2, t1], E[1, t2, t1], E[2, t2, t1]
+        out[r, 0] = x[0].ravel()[i] + k2 * np.dot(g, w[0]) + np.dot(g1, w[2])
+        out[r, 1] = x[1].ravel()[i] + k2 * np.dot(g, w[1]) + np.dot(g2, w[2])
+    return out
+
+
 def _circulant_spectra(n, k, quad, L):
     """FFT of the circulant embeddings (length L >= 2n-1 per axis) of G, G^1, G^2."""
     E = kernel_entries(n, k, quad)

@@ -1,4 +1,4 @@
-"""Python binding of libspm (include/spm.h): argument marshalling only.
+"""Python binding of libspm (include/spm.h, include/spm2d.h): argument marshalling only.
 
 Every computation runs in the CUDA library; this module converts numpy/torch
 arguments to pointers and status codes to exceptions.  Importing it loads
@@ -20,7 +20,7 @@ SPM_OK, SPM_ERR_INVALID_ARG, SPM_ERR_CUDA, SPM_ERR_OOM, SPM_ERR_NOT_BUILT, SPM_E
 SPM_QUAD_ORDER4, SPM_QUAD_ORDER2 = 0, 1
 SPM_C128, SPM_C64, SPM_MIXED, SPM_C64H = 0, 1, 2, 3
 
-# every symbol include/spm.h declares
+# every symbol include/spm.h and include/spm2d.h declare
 EXPORTS = [
     "spm_create_problem", "spm_destroy", "spm_problem_info", "spm_apply_A", "spm_apply_QA", "spm_apply_Q",
     "spm_build_stencils", "spm_set_stencils", "spm_get_stencils", "spm_factor_S", "spm_factor_S_tree", "spm_factor_info", "spm_device_status", "spm_selftest_bounded_wait", "spm_get_apply_plan", "spm_set_apply_plan", "spm_apply_S",
@@ -29,6 +29,10 @@ EXPORTS = [
     "spm_create_batch", "spm_destroy_batch", "spm_batch_size", "spm_batch_problem", "spm_batch_build_stencils",
     "spm_batch_apply_A", "spm_batch_solve", "spm_measure_peak", "spm_apply_A_cufft",
     "spm_save_apply_plans", "spm_load_apply_plans", "spm_profile_apply",
+    "spm2_create_problem", "spm2_destroy", "spm2_problem_info", "spm2_lattice_zeta_prime", "spm2_kernel_entries",
+    "spm2_apply_A", "spm2_apply_Q", "spm2_apply_QA", "spm2_build_stencils", "spm2_set_stencils",
+    "spm2_get_stencils", "spm2_apply_S", "spm2_factor_S", "spm2_factor_info", "spm2_solve_S",
+    "spm2_rhs_from_incident", "spm2_solve",
 ]
 
 
@@ -128,6 +132,22 @@ def _load():
         "spm_batch_apply_A": [P, I, P, P, P],
         "spm_batch_solve": [P, I, P, P, D, I, I, P],
         "spm_measure_peak": [I, ctypes.POINTER(D), ctypes.POINTER(D)],
+        "spm2_create_problem": [I, D, P, P, I, P, ctypes.POINTER(P)],
+        "spm2_destroy": [P],
+        "spm2_problem_info": [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(D)],
+        "spm2_kernel_entries": [P, P],
+        "spm2_apply_A": [P, I, P, P, I, P],
+        "spm2_apply_Q": [P, I, P, P, I, P],
+        "spm2_apply_QA": [P, I, P, P, I, P],
+        "spm2_build_stencils": [P, I],
+        "spm2_set_stencils": [P, P, P],
+        "spm2_get_stencils": [P, P, P, P],
+        "spm2_apply_S": [P, I, P, P, I, P],
+        "spm2_factor_S": [P, I],
+        "spm2_factor_info": [P, I, ctypes.POINTER(FactorReport)],
+        "spm2_solve_S": [P, I, P, P, I, P],
+        "spm2_rhs_from_incident": [P, P, P, I, P],
+        "spm2_solve": [P, I, P, P, I, D, I, I, ctypes.POINTER(SolveInfo)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -135,6 +155,8 @@ def _load():
         f.restype = I
     L.spm_lattice_constant.restype = D
     L.spm_lattice_constant.argtypes = []
+    L.spm2_lattice_zeta_prime.restype = D
+    L.spm2_lattice_zeta_prime.argtypes = []
     L.spm_last_error.restype = ctypes.c_char_p
     L.spm_last_error.argtypes = []
     return L
@@ -397,3 +419,109 @@ class Batch:
         if check:
             _check(st)
         return list(infos), st
+
+
+# ------------------------------------------------------------------ 2-D variant
+
+def _nrhs2(x, n):
+    return x.numel() // (2 * n * n)
+
+
+def spm2_lattice_zeta_prime() -> float:
+    return lib.spm2_lattice_zeta_prime()
+
+
+class Problem2D:
+    """Owns one spm2_problem handle (include/spm2d.h): the 2-D variant, two
+    unknowns per point on an n x n grid, fields [b][d][i2][i1]."""
+
+    def __init__(self, n, omega, eps, grad_eps, quad=SPM_QUAD_ORDER4, stream=None):
+        eps = np.ascontiguousarray(eps, dtype=np.complex128)
+        grad = np.ascontiguousarray(grad_eps, dtype=np.complex128)
+        if eps.size != n * n or grad.size != 2 * n * n:
+            raise ValueError("eps must have n^2 and grad_eps 2 n^2 entries")
+        h = ctypes.c_void_p()
+        _check(lib.spm2_create_problem(n, float(omega), _ptr(eps), _ptr(grad), quad, _stream(stream),
+                                       ctypes.byref(h)))
+        self.h = h
+        self.n = n
+        self.omega = float(omega)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.spm2_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        n, L, k = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        _check(lib.spm2_problem_info(self.h, ctypes.byref(n), ctypes.byref(L), ctypes.byref(k)))
+        return n.value, L.value, k.value
+
+    def kernel_entries(self):
+        W = 2 * self.n - 1
+        out = np.zeros((3, W, W), np.complex128)
+        _check(lib.spm2_kernel_entries(self.h, _ptr(out)))
+        return out
+
+    def apply_A(self, x, y, stream=None):
+        _check(lib.spm2_apply_A(self.h, _prec_of(x), _ptr(x), _ptr(y), _nrhs2(x, self.n), _stream(stream)))
+        return y
+
+    def apply_Q(self, v, y, stream=None):
+        _check(lib.spm2_apply_Q(self.h, _prec_of(v), _ptr(v), _ptr(y), _nrhs2(v, self.n), _stream(stream)))
+        return y
+
+    def apply_QA(self, x, y, stream=None):
+        _check(lib.spm2_apply_QA(self.h, _prec_of(x), _ptr(x), _ptr(y), _nrhs2(x, self.n), _stream(stream)))
+        return y
+
+    def build_stencils(self, factor_prec=SPM_C64):
+        _check(lib.spm2_build_stencils(self.h, factor_prec))
+
+    def set_stencils(self, alpha, beta):
+        a = np.ascontiguousarray(alpha, dtype=np.complex128)
+        b = np.ascontiguousarray(beta, dtype=np.complex128)
+        if a.size != 9 * 18 * 2 or b.size != 9 * 27 * 2:
+            raise ValueError("alpha must be [9][18][2] and beta [9][27][2]")
+        _check(lib.spm2_set_stencils(self.h, _ptr(a), _ptr(b)))
+
+    def get_stencils(self):
+        a = np.zeros((9, 18, 2), np.complex128)
+        b = np.zeros((9, 27, 2), np.complex128)
+        sv = np.zeros((9, 18), np.float64)
+        _check(lib.spm2_get_stencils(self.h, _ptr(a), _ptr(b), _ptr(sv)))
+        return a, b, sv
+
+    def apply_S(self, x, y, stream=None):
+        _check(lib.spm2_apply_S(self.h, _prec_of(x), _ptr(x), _ptr(y), _nrhs2(x, self.n), _stream(stream)))
+        return y
+
+    def factor_S(self, prec=SPM_C64):
+        _check(lib.spm2_factor_S(self.h, prec))
+
+    def factor_info(self, prec=SPM_C64):
+        r = FactorReport()
+        _check(lib.spm2_factor_info(self.h, prec, ctypes.byref(r)))
+        return r.variant, r.attempts, bool(r.half_store), r.probe_relres, r.raised_pivots
+
+    def solve_S(self, b, x, stream=None):
+        _check(lib.spm2_solve_S(self.h, _prec_of(b), _ptr(b), _ptr(x), _nrhs2(b, self.n), _stream(stream)))
+        return x
+
+    def rhs_from_incident(self, einc, g, stream=None):
+        _check(lib.spm2_rhs_from_incident(self.h, _ptr(einc), _ptr(g), _nrhs2(einc, self.n), _stream(stream)))
+        return g
+
+    def solve(self, g, x, prec=SPM_MIXED, tol=1e-6, maxit=500, restart=20, check=True):
+        info = SolveInfo()
+        st = lib.spm2_solve(self.h, prec, _ptr(g), _ptr(x), _nrhs2(g, self.n), float(tol), int(maxit), int(restart),
+                            ctypes.byref(info))
+        if check:
+            _check(st)
+        return info, st

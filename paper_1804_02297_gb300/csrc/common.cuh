@@ -161,6 +161,46 @@ struct spm_problem_s {
     DevBuf gmres_ws; // GMRES vectors and reductions of spm_solve
 };
 
+// ------------------------------------------------------------ sparse system
+// What the nested-dissection factor sees: a grid of n1 x n2 x n3 points (point
+// index (i3 n2 + i2) n1 + i1), D unknowns per point, couplings between points at
+// offsets in {-1,0,1}^3, stored as D x D blocks (row component c, column
+// component f, row-major) per point and offset: [point][nsten][D][D] with
+// nsten = 27 (offset s = (o1+1) + 3 (o2+1) + 9 (o3+1)) or, for a 2-D grid
+// (n3 = 1), nsten = 9 (s = (o1+1) + 3 (o2+1)).  A vector is [b][c][point].
+struct SparseSys {
+    int dims[3] = {0, 0, 0};
+    int D = 3, nsten = 27;
+    const void *S128 = nullptr, *S64 = nullptr;
+    cudaStream_t stream = nullptr;
+    NDFactor **slot128 = nullptr, **slot64 = nullptr;
+    spm_problem_s::FactorInfo *info = nullptr; // [0] complex128 factor, [1] complex64 factor
+    // y = S x in complex128 for one right-hand side (the factor's probe)
+    spm_status (*apply_S128)(void *ctx, const void *x, void *y, cudaStream_t s) = nullptr;
+    void *ctx = nullptr;
+    long points() const { return (long)dims[0] * dims[1] * dims[2]; }
+};
+spm_status spm_nd_factor(const SparseSys &S, int prec);
+spm_status spm_nd_factor_tree(const SparseSys &S, int prec, int variant);
+spm_status spm_nd_solve(NDFactor *F, int prec, const void *b, void *x, int nrhs, cudaStream_t s);
+
+// ------------------------------------------------------------ Krylov operators
+// The preconditioned GMRES driver (krylov.cu) sees the problem through these:
+// N unknowns per right-hand side, y = A x, y = Q v, x = S^{-1} b in the inner
+// precision (SPM_C128 / SPM_C64), and A x in complex128 for the true residual.
+struct KrylovOps {
+    long N = 0;
+    cudaStream_t stream = nullptr;
+    DevBuf *ws = nullptr; // GMRES workspace, kept by the problem
+    void *ctx = nullptr;
+    spm_status (*apply_A)(void *ctx, int prec, const void *x, void *y, int nrhs, cudaStream_t s) = nullptr;
+    spm_status (*apply_Q)(void *ctx, int prec, const void *v, void *y, int nrhs, cudaStream_t s) = nullptr;
+    spm_status (*solve_S)(void *ctx, int prec, const void *b, void *x, int nrhs, cudaStream_t s) = nullptr;
+};
+spm_status spm_gmres_solve(const KrylovOps &ops, int prec, const void *g, void *x, int nrhs, double tol, int maxit,
+                           int restart, spm_solve_info *info);
+spm_status spm_axpby_impl(int prec, long count, double a, const void *x, double b, void *y, cudaStream_t s);
+
 // ------------------------------------------------------------ internal API
 spm_status spm_apply_A_impl(spm_problem_s *P, int prec, const void *x, void *y, int nrhs, cudaStream_t s);
 spm_status spm_apply_Q_impl(spm_problem_s *P, int prec, const void *v, void *y, int nrhs, cudaStream_t s);

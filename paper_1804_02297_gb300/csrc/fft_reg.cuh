@@ -1,4 +1,4 @@
-// Register-resident Stockham FFT of one line of length L (a power of two, 8..512).
+// Register-resident Stockham FFT of one line of length L (a power of two, 8..2048).
 //
 // T = L/8 threads cooperate on a line; thread t holds v[m] = x[t + T m], m = 0..7,
 // both on entry and on exit, so loads and stores of a line are strided by T and
@@ -14,11 +14,14 @@
 
 namespace fftr {
 
-// stage radices: 8 | 8,2 | 8,4 | 8,8 | 8,8,2 | 8,8,4 | 8,8,8 for L = 8 ... 512
-__host__ __device__ constexpr int nstages(int L) { return L == 8 ? 1 : (L <= 64 ? 2 : 3); }
+// stage radices: 8 | 8,2 | 8,4 | 8,8 | 8,8,2 | 8,8,4 | 8,8,8 for L = 8 ... 512,
+// then 8,8,8,2 | 8,8,8,4 for L = 1024, 2048
+__host__ __device__ constexpr int nstages(int L) { return L == 8 ? 1 : (L <= 64 ? 2 : (L <= 512 ? 3 : 4)); }
 __host__ __device__ constexpr int radix_of(int L, int s)
 {
-    return s == 0 ? 8 : (s == 1 ? (L == 16 ? 2 : (L == 32 ? 4 : 8)) : (L == 128 ? 2 : (L == 256 ? 4 : 8)));
+    return s == 0 ? 8
+                  : (s == 1 ? (L == 16 ? 2 : (L == 32 ? 4 : 8))
+                            : (s == 2 ? (L == 128 ? 2 : (L == 256 ? 4 : 8)) : L / 512));
 }
 __host__ __device__ constexpr int span_of(int L, int s) { return s == 0 ? 1 : radix_of(L, s - 1) * span_of(L, s - 1); }
 
@@ -139,6 +142,7 @@ __device__ __forceinline__ void fft_line(C v[8], int t, Buf buf, Sync sync, cons
     dft<DIR, 8, PRUNE>(v); // stage 0: radix 8, span 1, no twiddles
     if constexpr (NS >= 2) stage<DIR, L, 1>(v, t, buf, sync, tw);
     if constexpr (NS >= 3) stage<DIR, L, 2>(v, t, buf, sync, tw);
+    if constexpr (NS >= 4) stage<DIR, L, 3>(v, t, buf, sync, tw);
     // last stage: v[u r + q] holds position t + T (u + (8/r) q); reorder to v[m]
     constexpr int rl = radix_of(L, NS - 1);
     if constexpr (rl != 8) {
@@ -199,6 +203,7 @@ __device__ __forceinline__ void fft_lines(C (&v)[K][8], int t, Buf buf, Sync syn
     for (int k = 0; k < K; ++k) dft<DIR, 8, PRUNE>(v[k]);
     if constexpr (NS >= 2) stage_k<DIR, L, 1, K>(v, t, buf, sync, tw);
     if constexpr (NS >= 3) stage_k<DIR, L, 2, K>(v, t, buf, sync, tw);
+    if constexpr (NS >= 4) stage_k<DIR, L, 3, K>(v, t, buf, sync, tw);
     constexpr int rl = radix_of(L, NS - 1);
     if constexpr (rl != 8) {
 #pragma unroll

@@ -317,21 +317,21 @@ __global__ void k_backsolve(GmresSmall gs, double2 *coef, int ld, int m, int res
 // guess: d = argmin over the Krylov space of ||S^{-1} Q (r - A d)||.  Stops
 // early when every active RHS reaches relative preconditioned residual rtol[b].
 template <typename R>
-spm_status gmres_cycle(spm_problem_s *P, int prec, const typename cplx_of<R>::type *r, typename cplx_of<R>::type *d,
-                       int nrhs, int restart, typename cplx_of<R>::type *V, typename cplx_of<R>::type *tmp,
-                       double2 *partial, double2 *h1, double2 *h2, double2 *nn, const GmresSmall &gs, int *count_host,
-                       int *iters, cudaStream_t s)
+spm_status gmres_cycle(const KrylovOps &ops, int prec, const typename cplx_of<R>::type *r,
+                       typename cplx_of<R>::type *d, int nrhs, int restart, typename cplx_of<R>::type *V,
+                       typename cplx_of<R>::type *tmp, double2 *partial, double2 *h1, double2 *h2, double2 *nn,
+                       const GmresSmall &gs, int *count_host, int *iters, cudaStream_t s)
 {
     using C = typename cplx_of<R>::type;
-    const long N = 3L * P->n * P->n * P->n;
+    const long N = ops.N;
     const long vstride = N * nrhs;
     const int ld = restart + 2;
     const unsigned sb = (unsigned)((nrhs + 63) / 64);
     C *w = V + (long)(restart)*vstride;
 
     // v0 = S^{-1} Q r / beta
-    SPM_TRY(spm_apply_Q_impl(P, prec, r, tmp, nrhs, s));
-    SPM_TRY(spm_solveS_impl(P, prec, tmp, V, nrhs, s));
+    SPM_TRY(ops.apply_Q(ops.ctx, prec, r, tmp, nrhs, s));
+    SPM_TRY(ops.solve_S(ops.ctx, prec, tmp, V, nrhs, s));
     SPM_TRY(dots<C>(V, vstride, 1, V, N, nrhs, partial, nn, ld, s));
     SPM_CUDA_TRY(cudaMemsetAsync(gs.count, 0, 2 * sizeof(int), s));
     k_cycle_init<<<sb, 64, 0, s>>>(gs, nn, ld, restart, nrhs);
@@ -342,9 +342,9 @@ spm_status gmres_cycle(spm_problem_s *P, int prec, const typename cplx_of<R>::ty
     for (; j < restart && count_host[0] > 0; ++j) {
         C *vj = V + (long)j * vstride;
         w = V + (long)(j + 1) * vstride;
-        SPM_TRY(spm_apply_A_impl(P, prec, vj, w, nrhs, s));        // w = A v_j
-        SPM_TRY(spm_apply_Q_impl(P, prec, w, tmp, nrhs, s));       // tmp = Q A v_j
-        SPM_TRY(spm_solveS_impl(P, prec, tmp, w, nrhs, s));        // w = S^{-1} Q A v_j
+        SPM_TRY(ops.apply_A(ops.ctx, prec, vj, w, nrhs, s));       // w = A v_j
+        SPM_TRY(ops.apply_Q(ops.ctx, prec, w, tmp, nrhs, s));      // tmp = Q A v_j
+        SPM_TRY(ops.solve_S(ops.ctx, prec, tmp, w, nrhs, s));      // w = S^{-1} Q A v_j
         // classical Gram-Schmidt twice, FP64 coefficients
         SPM_TRY(dots<C>(V, vstride, j + 1, w, N, nrhs, partial, h1, ld, s));
         SPM_TRY(axpy_multi<C>(V, vstride, j + 1, h1, ld, w, N, nrhs, -1.0, s));
@@ -382,13 +382,13 @@ spm_status norms(const C *v, long N, int nrhs, double2 *partial, double2 *hdev, 
 }
 
 template <typename R>
-spm_status solve_typed(spm_problem_s *P, int mode, const double2 *g, double2 *x, int nrhs, double tol, int maxit,
+spm_status solve_typed(const KrylovOps &ops, const double2 *g, double2 *x, int nrhs, double tol, int maxit,
                        int restart, spm_solve_info *info)
 {
     using C = typename cplx_of<R>::type;
     const int inner_prec = sizeof(R) == 8 ? SPM_C128 : SPM_C64;
-    cudaStream_t s = P->stream;
-    const long N = 3L * P->n * P->n * P->n;
+    cudaStream_t s = ops.stream;
+    const long N = ops.N;
     const long vstride = N * nrhs;
     const int ld = restart + 2;
     // workspace: r (c128), Ax (c128), V (restart+1), d, tmp (inner precision), reductions
@@ -396,7 +396,7 @@ spm_status solve_typed(spm_problem_s *P, int mode, const double2 *g, double2 *x,
                          sizeof(double) * 3 * (size_t)nrhs + sizeof(int) * ((size_t)nrhs + 2);
     size_t bytes = sizeof(double2) * 2 * vstride + sizeof(C) * (size_t)(restart + 3) * vstride +
                    sizeof(double2) * (size_t)nrhs * DOT_BLOCKS * VGROUP + small + 16 * 256;
-    DevBuf &ws = P->gmres_ws; // kept across solves: sized by the largest solve so far
+    DevBuf &ws = *ops.ws; // kept across solves: sized by the largest solve so far
     SPM_TRY(ws.ensure(bytes));
     char *p = ws.as<char>();
     double2 *r = reinterpret_cast<double2 *>(p); p += sizeof(double2) * vstride;
@@ -428,7 +428,7 @@ spm_status solve_typed(spm_problem_s *P, int mode, const double2 *g, double2 *x,
     double worst = 0.0;
     const double floor_rel = sizeof(R) == 8 ? 1e-14 : 2e-6;
     while (true) {
-        SPM_TRY(spm_apply_A_impl(P, SPM_C128, x, Ax, nrhs, s));
+        SPM_TRY(ops.apply_A(ops.ctx, SPM_C128, x, Ax, nrhs, s));
         SPM_CUDA_TRY(cudaMemcpyAsync(r, g, sizeof(double2) * vstride, cudaMemcpyDeviceToDevice, s));
         SPM_TRY(spm_axpby_impl(SPM_C128, vstride, -1.0, Ax, 1.0, r, s)); // r = g - A x
         SPM_TRY(norms<double2>(r, N, nrhs, partial, hdev, ld, rnorm, s));
@@ -455,7 +455,7 @@ spm_status solve_typed(spm_problem_s *P, int mode, const double2 *g, double2 *x,
         int it_cycle = 0;
         int cyc_restart = restart < maxit - iters ? restart : maxit - iters;
         SPM_CUDA_TRY(cudaMemcpyAsync(gs.rtol, rtol.data(), sizeof(double) * nrhs, cudaMemcpyHostToDevice, s));
-        SPM_TRY(gmres_cycle<R>(P, inner_prec, rin, d, nrhs, cyc_restart, V, tmp, partial, hdev, h2dev, nndev, gs,
+        SPM_TRY(gmres_cycle<R>(ops, inner_prec, rin, d, nrhs, cyc_restart, V, tmp, partial, hdev, h2dev, nndev, gs,
                                count_host, &it_cycle, s));
         iters += it_cycle;
         ++outer;
@@ -468,6 +468,31 @@ spm_status solve_typed(spm_problem_s *P, int mode, const double2 *g, double2 *x,
 
 } // namespace
 
+spm_status spm_gmres_solve(const KrylovOps &ops, int prec, const void *g, void *x, int nrhs, double tol, int maxit,
+                           int restart, spm_solve_info *info)
+{
+    const bool inner64 = prec != SPM_C128;
+    spm_status st = inner64 ? solve_typed<float>(ops, (const double2 *)g, (double2 *)x, nrhs, tol, maxit, restart, info)
+                            : solve_typed<double>(ops, (const double2 *)g, (double2 *)x, nrhs, tol, maxit, restart, info);
+    SPM_CUDA_TRY(cudaStreamSynchronize(ops.stream));
+    return st;
+}
+
+namespace {
+spm_status ops3_A(void *c, int prec, const void *x, void *y, int nrhs, cudaStream_t s)
+{
+    return spm_apply_A_impl(static_cast<spm_problem_s *>(c), prec, x, y, nrhs, s);
+}
+spm_status ops3_Q(void *c, int prec, const void *v, void *y, int nrhs, cudaStream_t s)
+{
+    return spm_apply_Q_impl(static_cast<spm_problem_s *>(c), prec, v, y, nrhs, s);
+}
+spm_status ops3_S(void *c, int prec, const void *b, void *x, int nrhs, cudaStream_t s)
+{
+    return spm_solveS_impl(static_cast<spm_problem_s *>(c), prec, b, x, nrhs, s);
+}
+} // namespace
+
 spm_status spm_solve_impl(spm_problem_s *P, int prec, const void *g, void *x, int nrhs, double tol, int maxit,
                           int restart, spm_solve_info *info)
 {
@@ -477,8 +502,13 @@ spm_status spm_solve_impl(spm_problem_s *P, int prec, const void *g, void *x, in
         spm_set_error("no factor of S in the %s precision (spm_factor_S)", inner64 ? "complex64" : "complex128");
         return SPM_ERR_NOT_BUILT;
     }
-    spm_status st = inner64 ? solve_typed<float>(P, prec, (const double2 *)g, (double2 *)x, nrhs, tol, maxit, restart, info)
-                            : solve_typed<double>(P, prec, (const double2 *)g, (double2 *)x, nrhs, tol, maxit, restart, info);
-    SPM_CUDA_TRY(cudaStreamSynchronize(P->stream));
-    return st;
+    KrylovOps ops;
+    ops.N = 3L * P->n * P->n * P->n;
+    ops.stream = P->stream;
+    ops.ws = &P->gmres_ws;
+    ops.ctx = P;
+    ops.apply_A = ops3_A;
+    ops.apply_Q = ops3_Q;
+    ops.solve_S = ops3_S;
+    return spm_gmres_solve(ops, prec, g, x, nrhs, tol, maxit, restart, info);
 }

@@ -3,8 +3,10 @@
 // algorithm"; complexity in Section 3.3).
 //
 // Geometric dissection: a box of grid points is cut by one plane normal to its
-// longest axis; one plane separates because S couples only points with
-// ||j - i||_inf <= 1.  Node = box B.  Its own unknowns are the separator plane
+// longest axis (a line on a 2-D grid); one plane separates because S couples
+// only points with ||j - i||_inf <= 1.  The grid, the unknowns per point and the
+// block layout of S come from a SparseSys (3-D: n^3 points, 3 unknowns, 27
+// neighbours; 2-D variant: n^2 points, 2 unknowns, 9 neighbours).  Node = box B.  Its own unknowns are the separator plane
 // (or every point of B for a leaf); its boundary unknowns are the points
 // outside B within distance 1 of B, which all lie on ancestor separators.  The
 // front is [own; boundary] x [own; boundary]:
@@ -53,30 +55,36 @@ struct Node {
 
 // ---------------------------------------------------------------- kernels
 
-// Assemble the own rows and own columns of S into a zeroed front (column-major, ld = f).
+// Assemble the own rows and own columns of S into a zeroed front (column-major,
+// ld = f); unknown (point a, component c) of the front is D a + c.
+struct GridDesc {
+    int n1, n2, n3, D, nsten;
+};
+
 template <typename C>
 __global__ void k_front_assemble(C *F, int f, const C *__restrict__ S, const int *__restrict__ own_pts, int nown,
-                                 const int *__restrict__ lmap, int e0, int e1, int e2, int ew0, int ew1, int n)
+                                 const int *__restrict__ lmap, int e0, int e1, int e2, int ew0, int ew1, GridDesc g)
 {
     int gid = blockIdx.x * blockDim.x + threadIdx.x;
-    if (gid >= nown * 27) return;
-    int a = gid / 27, s = gid % 27;
-    int o1 = s % 3 - 1, o2 = (s / 3) % 3 - 1, o3 = s / 9 - 1;
+    if (gid >= nown * g.nsten) return;
+    const int D = g.D, DD = g.D * g.D;
+    int a = gid / g.nsten, s = gid % g.nsten;
+    int o1 = s % 3 - 1, o2 = (s / 3) % 3 - 1, o3 = g.nsten == 27 ? s / 9 - 1 : 0;
     int i = own_pts[a];
-    int i1 = i % n, i2 = (i / n) % n, i3 = i / (n * n);
+    int i1 = i % g.n1, i2 = (i / g.n1) % g.n2, i3 = i / (g.n1 * g.n2);
     int j1 = i1 + o1, j2 = i2 + o2, j3 = i3 + o3;
-    if (j1 < 0 || j2 < 0 || j3 < 0 || j1 >= n || j2 >= n || j3 >= n) return;
+    if (j1 < 0 || j2 < 0 || j3 < 0 || j1 >= g.n1 || j2 >= g.n2 || j3 >= g.n3) return;
     int lj = lmap[((j3 - e2) * ew1 + (j2 - e1)) * ew0 + (j1 - e0)];
     if (lj < 0) return; // neighbour eliminated in a child subtree
-    long j = ((long)j3 * n + j2) * n + j1;
-    const C *blk = S + ((long)i * 27 + s) * 9; // rows (i,c), columns (j,f)
-    for (int c = 0; c < 3; ++c)
-        for (int q = 0; q < 3; ++q) F[(long)(3 * lj + q) * f + 3 * a + c] = blk[c * 3 + q];
+    long j = ((long)j3 * g.n2 + j2) * g.n1 + j1;
+    const C *blk = S + ((long)i * g.nsten + s) * DD; // rows (i,c), columns (j,f)
+    for (int c = 0; c < D; ++c)
+        for (int q = 0; q < D; ++q) F[(long)(D * lj + q) * f + D * a + c] = blk[c * D + q];
     if (lj >= nown) { // row of a boundary unknown j, column of own unknown i
-        int sr = 26 - s; // offset -o
-        const C *bj = S + (j * 27 + sr) * 9;
-        for (int c = 0; c < 3; ++c)
-            for (int q = 0; q < 3; ++q) F[(long)(3 * a + q) * f + 3 * lj + c] = bj[c * 3 + q];
+        int sr = g.nsten - 1 - s; // offset -o
+        const C *bj = S + (j * g.nsten + sr) * DD;
+        for (int c = 0; c < D; ++c)
+            for (int q = 0; q < D; ++q) F[(long)(D * a + q) * f + D * lj + c] = bj[c * D + q];
     }
 }
 
@@ -250,8 +258,8 @@ __device__ __forceinline__ int find_node(const long *__restrict__ unit, int nn, 
 // packed input of every node of a level: own (which = 0) or boundary (1) unknowns of w
 template <typename C>
 __global__ void k_level_gather(C *packed, const C *__restrict__ w, const LevelNode *__restrict__ nodes,
-                               const long *__restrict__ in_units, const int *__restrict__ pts, int nn, long n3,
-                               int nrhs, int which)
+                               const long *__restrict__ in_units, const int *__restrict__ pts, int nn, long npts,
+                               int D, int nrhs, int which)
 {
     long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= in_units[nn] * nrhs) return;
@@ -259,16 +267,16 @@ __global__ void k_level_gather(C *packed, const C *__restrict__ w, const LevelNo
     const LevelNode nd = nodes[id];
     long e = gid - in_units[id] * nrhs;
     long r = e % nd.cols, b = e / nd.cols;
-    int pt = pts[(which ? nd.bnd_pts : nd.own_pts) + (int)(r / 3)];
-    packed[gid] = w[(b * 3 + (r % 3)) * n3 + pt];
+    int pt = pts[(which ? nd.bnd_pts : nd.own_pts) + (int)(r / D)];
+    packed[gid] = w[(b * D + (r % D)) * npts + pt];
 }
 
 // forward (mode 0): w_own = out[0:o3], w_bnd -= out[o3:] (siblings share
 // boundaries: atomic); backward (mode 1): w_own -= out
 template <typename C>
 __global__ void k_level_scatter(C *w, const C *__restrict__ packed, const LevelNode *__restrict__ nodes,
-                                const long *__restrict__ out_units, const int *__restrict__ pts, int nn, long n3,
-                                int nrhs, int mode)
+                                const long *__restrict__ out_units, const int *__restrict__ pts, int nn, long npts,
+                                int D, int nrhs, int mode)
 {
     long gid = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (gid >= out_units[nn] * nrhs) return;
@@ -277,9 +285,9 @@ __global__ void k_level_scatter(C *w, const C *__restrict__ packed, const LevelN
     long e = gid - out_units[id] * nrhs;
     long r = e % nd.rows, b = e / nd.rows;
     C v = packed[gid];
-    const int o3 = 3 * nd.nown;
+    const int o3 = D * nd.nown;
     if (r < o3) {
-        long g = (b * 3 + (r % 3)) * n3 + pts[nd.own_pts + (int)(r / 3)];
+        long g = (b * D + (r % D)) * npts + pts[nd.own_pts + (int)(r / D)];
         if (mode == 0) {
             w[g] = v;
         } else {
@@ -290,7 +298,7 @@ __global__ void k_level_scatter(C *w, const C *__restrict__ packed, const LevelN
         }
     } else {
         long rb = r - o3;
-        long g = (b * 3 + (rb % 3)) * n3 + pts[nd.bnd_pts + (int)(rb / 3)];
+        long g = (b * D + (rb % D)) * npts + pts[nd.bnd_pts + (int)(rb / D)];
         atomicAdd(&w[g].x, -v.x);
         atomicAdd(&w[g].y, -v.y);
     }
@@ -307,7 +315,8 @@ struct NDFactor {
     size_t stored_bytes = 0; // bytes of the stored blocks (G and X, plus half-storage scales)
     bool half_store = false; // blocks as scaled binary16 pairs (complex64 factor only)
     DevBuf scales;           // per-column scales (half storage)
-    int n = 0;
+    int D = 3;               // unknowns per point
+    long npts = 0;           // grid points
     std::vector<Node> nodes; // post-order
     DevBuf pts, maps, rels;  // int lists
     DevBuf fac;              // persistent: per node [F11;F21] (f x nown3) then X (nown3 x nbnd3)
@@ -393,16 +402,16 @@ int build_tree(std::vector<Node> &nodes, const int lo[3], const int hi[3], int v
 } // namespace
 
 template <typename R>
-static spm_status factor_typed(spm_problem_s *P, NDFactor *F, bool half_store, int variant)
+static spm_status factor_typed(const SparseSys &SY, NDFactor *F, bool half_store, int variant)
 {
     using C = typename cplx_of<R>::type;
-    using CV = typename cplx_of<R>::type;
-    const int n = P->n;
-    const long n3 = (long)n * n * n;
-    cudaStream_t s = P->stream;
-    F->n = n;
+    const int n1 = SY.dims[0], n2 = SY.dims[1], n3d = SY.dims[2], D = SY.D;
+    const GridDesc gd{n1, n2, n3d, D, SY.nsten};
+    cudaStream_t s = SY.stream;
+    F->D = D;
+    F->npts = SY.points();
     F->nodes.clear();
-    int lo[3] = {0, 0, 0}, hi[3] = {n, n, n};
+    int lo[3] = {0, 0, 0}, hi[3] = {n1, n2, n3d};
     build_tree(F->nodes, lo, hi, variant);
     F->variant = variant;
     std::vector<Node> &nodes = F->nodes;
@@ -417,16 +426,16 @@ static spm_status factor_typed(spm_problem_s *P, NDFactor *F, bool half_store, i
         if (nd.axis >= 0) { olo[nd.axis] = nd.cut; ohi[nd.axis] = nd.cut + 1; }
         for (int z = olo[2]; z < ohi[2]; ++z)
             for (int y = olo[1]; y < ohi[1]; ++y)
-                for (int x = olo[0]; x < ohi[0]; ++x) pts.push_back((z * n + y) * n + x);
+                for (int x = olo[0]; x < ohi[0]; ++x) pts.push_back((z * n2 + y) * n1 + x);
         nd.nown = (int)(pts.size() - nd.own_off);
         nd.bnd_off = pts.size();
-        for (int d = 0; d < 3; ++d) { nd.elo[d] = std::max(nd.lo[d] - 1, 0); nd.ehi[d] = std::min(nd.hi[d] + 1, n); }
+        for (int d = 0; d < 3; ++d) { nd.elo[d] = std::max(nd.lo[d] - 1, 0); nd.ehi[d] = std::min(nd.hi[d] + 1, hi[d]); }
         for (int z = nd.elo[2]; z < nd.ehi[2]; ++z)
             for (int y = nd.elo[1]; y < nd.ehi[1]; ++y)
                 for (int x = nd.elo[0]; x < nd.ehi[0]; ++x) {
                     bool inside = x >= nd.lo[0] && x < nd.hi[0] && y >= nd.lo[1] && y < nd.hi[1] && z >= nd.lo[2] &&
                                   z < nd.hi[2];
-                    if (!inside) pts.push_back((z * n + y) * n + x);
+                    if (!inside) pts.push_back((z * n2 + y) * n1 + x);
                 }
         nd.nbnd = (int)(pts.size() - nd.bnd_off);
         // local map over the expanded box: own -> [0,nown), bnd -> nown + rank, else -1
@@ -435,7 +444,7 @@ static spm_status factor_typed(spm_problem_s *P, NDFactor *F, bool half_store, i
         size_t base = maps.size();
         maps.resize(base + (size_t)ew[0] * ew[1] * ew[2], -1);
         auto mi = [&](int p) {
-            int x = p % n, y = (p / n) % n, z = p / (n * n);
+            int x = p % n1, y = (p / n1) % n2, z = p / (n1 * n2);
             return base + ((size_t)(z - nd.elo[2]) * ew[1] + (y - nd.elo[1])) * ew[0] + (x - nd.elo[0]);
         };
         for (int a = 0; a < nd.nown; ++a) maps[mi(pts[nd.own_off + a])] = a;
@@ -451,10 +460,10 @@ static spm_status factor_typed(spm_problem_s *P, NDFactor *F, bool half_store, i
             int ew[3] = {nd.ehi[0] - nd.elo[0], nd.ehi[1] - nd.elo[1], nd.ehi[2] - nd.elo[2]};
             for (int b = 0; b < c.nbnd; ++b) {
                 int p = pts[c.bnd_off + b];
-                int x = p % n, y = (p / n) % n, z = p / (n * n);
+                int x = p % n1, y = (p / n1) % n2, z = p / (n1 * n2);
                 int l = maps[nd.map_off + ((size_t)(z - nd.elo[2]) * ew[1] + (y - nd.elo[1])) * ew[0] + (x - nd.elo[0])];
                 if (l < 0) { spm_set_error("nested dissection: child boundary point outside the parent front"); return SPM_ERR_NUMERICAL; }
-                for (int q = 0; q < 3; ++q) rels.push_back(3 * l + q);
+                for (int q = 0; q < D; ++q) rels.push_back(D * l + q);
             }
         }
     }
@@ -464,7 +473,7 @@ static spm_status factor_typed(spm_problem_s *P, NDFactor *F, bool half_store, i
     std::vector<size_t> upd_size(NN, 0);
     for (int id = 0; id < NN; ++id) {
         Node &nd = nodes[id];
-        long o3 = 3L * nd.nown, b3 = 3L * nd.nbnd, f = o3 + b3;
+        long o3 = (long)D * nd.nown, b3 = (long)D * nd.nbnd, f = o3 + b3;
         nd.fac_off = fac_total;
         fac_total += f * o3 + o3 * b3;
         nd.piv_off = piv_total;
@@ -487,7 +496,7 @@ static spm_status factor_typed(spm_problem_s *P, NDFactor *F, bool half_store, i
     std::vector<int> parent(NN, -1);
     for (int id = 0; id < NN; ++id) { // postorder: children before parents
         const Node &nd = nodes[id];
-        smax[id] = 3 * (size_t)nd.nown;
+        smax[id] = D * (size_t)nd.nown;
         for (int ch : {nd.left, nd.right})
             if (ch >= 0) { smax[id] = std::max(smax[id], smax[ch]); parent[ch] = id; }
     }
@@ -524,7 +533,7 @@ static spm_status factor_typed(spm_problem_s *P, NDFactor *F, bool half_store, i
     size_t root_upd_total = 0;
     for (int id = 0; id < NN; ++id) {
         const Node &nd = nodes[id];
-        const size_t o3 = 3 * (size_t)nd.nown, b3 = 3 * (size_t)nd.nbnd, f = o3 + b3;
+        const size_t o3 = D * (size_t)nd.nown, b3 = D * (size_t)nd.nbnd, f = o3 + b3;
         const int g = slot(id);
         g_front[g] = std::max(g_front[g], f * f);
         g_gx[g] = std::max(g_gx[g], f * o3 + o3 * b3);
@@ -539,7 +548,7 @@ static spm_status factor_typed(spm_problem_s *P, NDFactor *F, bool half_store, i
         }
     }
     F->max_front_unknowns = 0;
-    for (const Node &nd : nodes) F->max_front_unknowns = std::max(F->max_front_unknowns, (size_t)(3 * (nd.nown + nd.nbnd)));
+    for (const Node &nd : nodes) F->max_front_unknowns = std::max(F->max_front_unknowns, (size_t)(D * (nd.nown + nd.nbnd)));
     SPM_TRY(F->pts.ensure(sizeof(int) * pts.size()));
     SPM_TRY(F->maps.ensure(sizeof(int) * maps.size()));
     SPM_TRY(F->rels.ensure(sizeof(int) * std::max<size_t>(rels.size(), 1)));
@@ -588,7 +597,7 @@ static spm_status factor_typed(spm_problem_s *P, NDFactor *F, bool half_store, i
     }
     cudaEventDestroy(start_ev);
 
-    const C *Sdev = reinterpret_cast<const C *>(sizeof(R) == 8 ? P->S128.ptr : P->S64.ptr);
+    const C *Sdev = reinterpret_cast<const C *>(sizeof(R) == 8 ? SY.S128 : SY.S64);
     const int *dpts = F->pts.as<int>(), *dmaps = F->maps.as<int>(), *drels = F->rels.as<int>();
     C *fac = F->fac.as<C>();
     int *dinfo = F->info.as<int>();
@@ -600,17 +609,17 @@ static spm_status factor_typed(spm_problem_s *P, NDFactor *F, bool half_store, i
         Slot &sl = slots[g];
         cudaStream_t ss = sl.st ? sl.st : s;
         C *front = sl.front.as<C>(), *stack = sl.stack.as<C>();
-        const int o3 = 3 * nd.nown, b3 = 3 * nd.nbnd, f = o3 + b3;
+        const int o3 = D * nd.nown, b3 = D * nd.nbnd, f = o3 + b3;
         k_zero<C><<<blocks((long)f * f), 256, 0, ss>>>(front, (long)f * f);
         int ew0 = nd.ehi[0] - nd.elo[0], ew1 = nd.ehi[1] - nd.elo[1];
-        k_front_assemble<C><<<blocks((long)nd.nown * 27), 256, 0, ss>>>(front, f, Sdev, dpts + nd.own_off, nd.nown,
-                                                                         dmaps + nd.map_off, nd.elo[0], nd.elo[1],
-                                                                         nd.elo[2], ew0, ew1, n);
+        k_front_assemble<C><<<blocks((long)nd.nown * gd.nsten), 256, 0, ss>>>(front, f, Sdev, dpts + nd.own_off,
+                                                                               nd.nown, dmaps + nd.map_off, nd.elo[0],
+                                                                               nd.elo[1], nd.elo[2], ew0, ew1, gd);
         // extend-add the children's updates
         for (int ch : {nd.left, nd.right}) {
             if (ch < 0) continue;
             Node &c = nodes[ch];
-            int bc = 3 * c.nbnd;
+            int bc = D * c.nbnd;
             if (bc == 0) continue;
             k_extend_add<C><<<blocks((long)bc * bc), 256, 0, ss>>>(front, f, upd_ptr[ch], bc, drels + c.rel_off);
         }
@@ -686,7 +695,7 @@ static spm_status factor_typed(spm_problem_s *P, NDFactor *F, bool half_store, i
             nn = 0;
             for (int id : ids) {
                 const Node &nd = nodes[id];
-                const int o3 = 3 * nd.nown, b3 = 3 * nd.nbnd, f = o3 + b3;
+                const int o3 = D * nd.nown, b3 = D * nd.nbnd, f = o3 + b3;
                 LevelNode L;
                 L.rows = fwd ? f : o3;
                 L.cols = fwd ? o3 : b3;
@@ -734,19 +743,17 @@ static spm_status factor_typed(spm_problem_s *P, NDFactor *F, bool half_store, i
         if (!tt.empty())
             SPM_CUDA_TRY(cudaMemcpy(F->lv_tiles.ptr, tt.data(), sizeof(Tile) * tt.size(), cudaMemcpyHostToDevice));
     }
-    (void)n3;
-    (void)sizeof(CV);
     return SPM_OK;
 }
 
 template <typename R>
-static spm_status solve_typed(spm_problem_s *P, NDFactor *F, const void *bv, void *xv, int nrhs, cudaStream_t s)
+static spm_status solve_typed(NDFactor *F, const void *bv, void *xv, int nrhs, cudaStream_t s)
 {
     using C = typename cplx_of<R>::type;
-    const int n = P->n;
-    const long n3 = (long)n * n * n;
+    const long npts = F->npts;
+    const int D = F->D;
     C *x = reinterpret_cast<C *>(xv);
-    SPM_CUDA_TRY(cudaMemcpyAsync(x, bv, sizeof(C) * 3 * n3 * nrhs, cudaMemcpyDeviceToDevice, s));
+    SPM_CUDA_TRY(cudaMemcpyAsync(x, bv, sizeof(C) * D * npts * nrhs, cudaMemcpyDeviceToDevice, s));
     const size_t pin = (size_t)F->max_pack_in * nrhs, pout = (size_t)F->max_pack_out * nrhs;
     SPM_TRY(F->solve_ws.ensure(sizeof(C) * (pin + pout)));
     C *in = F->solve_ws.as<C>();
@@ -783,21 +790,21 @@ static spm_status solve_typed(spm_problem_s *P, NDFactor *F, const void *bv, voi
         const NDFactor::Level &lv = F->levels[l];
         if (lv.nn_f == 0) continue;
         k_level_gather<C><<<blocks(lv.pack_f_in * nrhs), 256, 0, s>>>(in, x, tn + lv.nodes_f, tu + lv.units_f_in, dpts,
-                                                                       lv.nn_f, n3, nrhs, 0);
+                                                                       lv.nn_f, npts, D, nrhs, 0);
         SPM_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(C) * lv.pack_f_out * nrhs, s));
         gemv(lv.ntiles_f, tn + lv.nodes_f, tt + lv.tiles_f);
         k_level_scatter<C><<<blocks(lv.pack_f_out * nrhs), 256, 0, s>>>(x, out, tn + lv.nodes_f, tu + lv.units_f_out,
-                                                                         dpts, lv.nn_f, n3, nrhs, 0);
+                                                                         dpts, lv.nn_f, npts, D, nrhs, 0);
     }
     for (int l = NL - 1; l >= 0; --l) { // backward, root first
         const NDFactor::Level &lv = F->levels[l];
         if (lv.nn_b == 0) continue;
         k_level_gather<C><<<blocks(lv.pack_b_in * nrhs), 256, 0, s>>>(in, x, tn + lv.nodes_b, tu + lv.units_b_in, dpts,
-                                                                       lv.nn_b, n3, nrhs, 1);
+                                                                       lv.nn_b, npts, D, nrhs, 1);
         SPM_CUDA_TRY(cudaMemsetAsync(out, 0, sizeof(C) * lv.pack_b_out * nrhs, s));
         gemv(lv.ntiles_b, tn + lv.nodes_b, tt + lv.tiles_b);
         k_level_scatter<C><<<blocks(lv.pack_b_out * nrhs), 256, 0, s>>>(x, out, tn + lv.nodes_b, tu + lv.units_b_out,
-                                                                         dpts, lv.nn_b, n3, nrhs, 1);
+                                                                         dpts, lv.nn_b, npts, D, nrhs, 1);
     }
     SPM_CUDA_TRY(cudaGetLastError());
     return SPM_OK;
@@ -849,10 +856,10 @@ __global__ void k_resid_norms(const double2 *y, const double2 *b, long N, double
 
 // ||S x - b|| / ||b|| for x = S^{-1} b through the factor of precision `prec`,
 // with b a fixed pseudo-random vector and S x formed in complex128.
-spm_status probe_factor(spm_problem_s *P, int prec, double *relres)
+spm_status probe_factor(const SparseSys &SY, int prec, double *relres)
 {
-    const long N = 3L * P->n * P->n * P->n;
-    cudaStream_t s = P->stream;
+    const long N = (long)SY.D * SY.points();
+    cudaStream_t s = SY.stream;
     DevBuf buf;
     SPM_TRY(buf.ensure(sizeof(double2) * 3 * N + sizeof(float2) * 2 * N + 2 * sizeof(double)));
     double2 *b = buf.as<double2>(), *x = b + N, *y = x + N;
@@ -862,12 +869,12 @@ spm_status probe_factor(spm_problem_s *P, int prec, double *relres)
     const unsigned g = (unsigned)((N + 255) / 256);
     k_probe_rhs<<<g, 256, 0, s>>>(b, single ? b64 : nullptr, N);
     if (single) {
-        SPM_TRY(spm_solveS_impl(P, SPM_C64, b64, x64, 1, s));
+        SPM_TRY(spm_nd_solve(*SY.slot64, SPM_C64, b64, x64, 1, s));
         k_widen<<<g, 256, 0, s>>>(x64, x, N);
     } else {
-        SPM_TRY(spm_solveS_impl(P, SPM_C128, b, x, 1, s));
+        SPM_TRY(spm_nd_solve(*SY.slot128, SPM_C128, b, x, 1, s));
     }
-    SPM_TRY(spm_apply_S_impl(P, SPM_C128, x, y, 1, s));
+    SPM_TRY(SY.apply_S128(SY.ctx, x, y, s));
     SPM_CUDA_TRY(cudaMemsetAsync(acc, 0, 2 * sizeof(double), s));
     k_resid_norms<<<1024, 256, 0, s>>>(y, b, N, acc);
     double h[2];
@@ -887,14 +894,14 @@ double probe_accept(int prec)
     return prec == SPM_C128 ? 1e-6 : (prec == SPM_C64H ? 3e-1 : 3e-2);
 }
 
-spm_status factor_once(spm_problem_s *P, int prec, int variant, NDFactor *&slot)
+spm_status factor_once(const SparseSys &SY, int prec, int variant, NDFactor *&slot)
 {
     spm_factor_free(slot);
     slot = nullptr;
     NDFactor *F = new NDFactor();
     F->prec = prec == SPM_C128 ? SPM_C128 : SPM_C64;
-    spm_status st = prec == SPM_C128 ? factor_typed<double>(P, F, false, variant)
-                                     : factor_typed<float>(P, F, prec == SPM_C64H, variant);
+    spm_status st = prec == SPM_C128 ? factor_typed<double>(SY, F, false, variant)
+                                     : factor_typed<float>(SY, F, prec == SPM_C64H, variant);
     if (st != SPM_OK) {
         delete F;
         return st;
@@ -907,55 +914,92 @@ spm_status factor_once(spm_problem_s *P, int prec, int variant, NDFactor *&slot)
 
 // Factor, probe the factor's accuracy, and if the probe residual is above the
 // acceptance level try the other tree variants, keeping the most accurate.
-spm_status spm_factor_impl(spm_problem_s *P, int prec)
+spm_status spm_nd_factor(const SparseSys &SY, int prec)
 {
     const int fi = prec == SPM_C128 ? 0 : 1;
-    NDFactor *&slot = fi == 0 ? P->fac128 : P->fac64;
+    NDFactor *&slot = fi == 0 ? *SY.slot128 : *SY.slot64;
     int best_v = -1, attempts = 0;
     double best = HUGE_VAL, last = HUGE_VAL;
     for (int v = 0; v < TREE_VARIANTS; ++v) {
-        SPM_TRY(factor_once(P, prec, v, slot));
+        SPM_TRY(factor_once(SY, prec, v, slot));
         ++attempts;
-        SPM_TRY(probe_factor(P, prec, &last));
+        SPM_TRY(probe_factor(SY, prec, &last));
         if (last < best) { best = last; best_v = v; }
         if (last <= probe_accept(prec)) break;
     }
     if (best_v != slot->variant) { // a later variant was worse: rebuild the best one
-        SPM_TRY(factor_once(P, prec, best_v, slot));
+        SPM_TRY(factor_once(SY, prec, best_v, slot));
         ++attempts;
     }
-    P->fac_info[fi].variant = best_v;
-    P->fac_info[fi].attempts = attempts;
-    P->fac_info[fi].raised_pivots = slot->raised_pivots;
-    P->fac_info[fi].stored_bytes = slot->stored_bytes;
-    P->fac_info[fi].probe_relres = best;
-    P->fac_info[fi].half_store = prec == SPM_C64H;
+    SY.info[fi].variant = best_v;
+    SY.info[fi].attempts = attempts;
+    SY.info[fi].raised_pivots = slot->raised_pivots;
+    SY.info[fi].stored_bytes = slot->stored_bytes;
+    SY.info[fi].probe_relres = best;
+    SY.info[fi].half_store = prec == SPM_C64H;
     return SPM_OK;
 }
 
 // Factor on one given tree variant (no retry); the probe is still recorded.
-spm_status spm_factor_tree_impl(spm_problem_s *P, int prec, int variant)
+spm_status spm_nd_factor_tree(const SparseSys &SY, int prec, int variant)
 {
     if (variant < 0 || variant >= TREE_VARIANTS) {
         spm_set_error("tree variant must be in [0, %d)", TREE_VARIANTS);
         return SPM_ERR_INVALID_ARG;
     }
     const int fi = prec == SPM_C128 ? 0 : 1;
-    NDFactor *&slot = fi == 0 ? P->fac128 : P->fac64;
-    SPM_TRY(factor_once(P, prec, variant, slot));
+    NDFactor *&slot = fi == 0 ? *SY.slot128 : *SY.slot64;
+    SPM_TRY(factor_once(SY, prec, variant, slot));
     double r = 0;
-    SPM_TRY(probe_factor(P, prec, &r));
-    P->fac_info[fi].variant = variant;
-    P->fac_info[fi].attempts = 1;
-    P->fac_info[fi].raised_pivots = slot->raised_pivots;
-    P->fac_info[fi].stored_bytes = slot->stored_bytes;
-    P->fac_info[fi].probe_relres = r;
-    P->fac_info[fi].half_store = prec == SPM_C64H;
+    SPM_TRY(probe_factor(SY, prec, &r));
+    SY.info[fi].variant = variant;
+    SY.info[fi].attempts = 1;
+    SY.info[fi].raised_pivots = slot->raised_pivots;
+    SY.info[fi].stored_bytes = slot->stored_bytes;
+    SY.info[fi].probe_relres = r;
+    SY.info[fi].half_store = prec == SPM_C64H;
     return SPM_OK;
+}
+
+spm_status spm_nd_solve(NDFactor *F, int prec, const void *b, void *x, int nrhs, cudaStream_t s)
+{
+    if (!F) { spm_set_error("no factor of S in this precision"); return SPM_ERR_NOT_BUILT; }
+    return prec == SPM_C128 ? solve_typed<double>(F, b, x, nrhs, s) : solve_typed<float>(F, b, x, nrhs, s);
+}
+
+// ---------------------------------------------------------------- 3-D problem
+namespace {
+spm_status apply_S128_3d(void *ctx, const void *x, void *y, cudaStream_t s)
+{
+    return spm_apply_S_impl(static_cast<spm_problem_s *>(ctx), SPM_C128, x, y, 1, s);
+}
+
+SparseSys sys_of(spm_problem_s *P)
+{
+    SparseSys S;
+    S.dims[0] = S.dims[1] = S.dims[2] = P->n;
+    S.D = 3;
+    S.nsten = 27;
+    S.S128 = P->S128.ptr;
+    S.S64 = P->S64.ptr;
+    S.stream = P->stream;
+    S.slot128 = &P->fac128;
+    S.slot64 = &P->fac64;
+    S.info = P->fac_info;
+    S.apply_S128 = apply_S128_3d;
+    S.ctx = P;
+    return S;
+}
+} // namespace
+
+spm_status spm_factor_impl(spm_problem_s *P, int prec) { return spm_nd_factor(sys_of(P), prec); }
+
+spm_status spm_factor_tree_impl(spm_problem_s *P, int prec, int variant)
+{
+    return spm_nd_factor_tree(sys_of(P), prec, variant);
 }
 
 spm_status spm_solveS_impl(spm_problem_s *P, int prec, const void *b, void *x, int nrhs, cudaStream_t s)
 {
-    NDFactor *F = prec == SPM_C128 ? P->fac128 : P->fac64;
-    return prec == SPM_C128 ? solve_typed<double>(P, F, b, x, nrhs, s) : solve_typed<float>(P, F, b, x, nrhs, s);
+    return spm_nd_solve(prec == SPM_C128 ? P->fac128 : P->fac64, prec, b, x, nrhs, s);
 }

@@ -1,4 +1,4 @@
-"""The C-ABI library builds, loads and exports every symbol include/spm.h declares.
+"""The C-ABI library builds, loads and exports every symbol include/*.h declares.
 
 No compute call runs here (no GPU on the build host): only symbol lookup, the
 host-side lattice constant and argument checks that return before any CUDA call.
@@ -22,9 +22,14 @@ def spm():
 
 
 def declared_symbols():
-    src = open(os.path.join(ROOT, "include", "spm.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(spm_[a-z_A-Z0-9]+)\s*\(", src)))
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(spm2?_[a-z_A-Z0-9]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_every_declared_symbol_is_exported(spm):
@@ -76,3 +81,24 @@ def test_host_side_settings_without_gpu(spm):
     assert lib.spm_factor_info(None, spm.SPM_C64, ctypes.byref(rep)) == spm.SPM_ERR_INVALID_ARG
     assert lib.spm_device_status(None) == spm.SPM_ERR_INVALID_ARG
     assert lib.spm_selftest_bounded_wait(None) == spm.SPM_ERR_INVALID_ARG
+
+
+def test_2d_lattice_constant_matches_oracle(spm):
+    """Z'(0) of the Z^2 lattice zeta: library host arithmetic and oracle agree."""
+    from oracle import twod
+    assert abs(spm.spm2_lattice_zeta_prime() - twod.lattice_zeta_prime0()) < 1e-14
+
+
+def test_2d_argument_validation_without_gpu(spm):
+    lib = spm.lib
+    h = ctypes.c_void_p()
+    eps = np.ones(9, np.complex128)
+    grad = np.zeros(18, np.complex128)
+    assert lib.spm2_create_problem(3, 1.0, spm._ptr(eps), spm._ptr(grad), 0, None, ctypes.byref(h)) == spm.SPM_ERR_INVALID_ARG
+    assert b"outside" in lib.spm_last_error()
+    eps = np.ones(16, np.complex128)
+    assert lib.spm2_create_problem(4, 1.0, spm._ptr(eps), None, 0, None, ctypes.byref(h)) == spm.SPM_ERR_INVALID_ARG
+    eps[3] = 0
+    grad = np.zeros(32, np.complex128)
+    assert lib.spm2_create_problem(4, 1.0, spm._ptr(eps), spm._ptr(grad), 0, None, ctypes.byref(h)) == spm.SPM_ERR_INVALID_ARG
+    assert lib.spm2_apply_A(None, 0, None, None, 1, None) == spm.SPM_ERR_INVALID_ARG
