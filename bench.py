@@ -74,7 +74,7 @@ def parse():
                     help="uneven32: also solve the n = 96 problems, one after another")
     ap.add_argument("--uneven-n96-factor", default="c64", choices=["c64", "c64h"],
                     help="uneven32 --uneven-solve-all: factor of the n = 96 problems (complex64 or half storage)")
-    ap.add_argument("--profile-case", default=None, choices=["qa64", "a128", "a256"],
+    ap.add_argument("--profile-case", default=None, choices=["qa64", "a128", "a256", "2d959", "2d959c128", "2d119"],
                     help="small fixed case for ncu captures: a few applies (Q A at n = 64 with seeded random "
                          "stencil tables, no factor; or A at n = 128 / 256) with the z-pass plan --zplan, no timing")
     ap.add_argument("--zplan", type=int, default=0, help="apply-plan variant for --profile-case")
@@ -90,6 +90,20 @@ def run_profile_case(args):
     their values, and the 26 GB factor of the full bench stays out of the capture."""
     import torch
     import paper_1804_02297_gb300 as spm
+    if args.profile_case.startswith("2d"):
+        # the 2-D variant's apply of A: lens medium at n = 959 (L = 2048) or 119 (L = 256), one RHS
+        n = 119 if args.profile_case == "2d119" else 959
+        wl = si.workload_2d(f"lens2d_n{n}")
+        P = spm.Problem2D(n, wl["omega"], wl["eps"], wl["grad"])
+        dt = torch.complex128 if args.profile_case.endswith("c128") else torch.complex64
+        x = torch.from_numpy(wl["einc"]).to(dt).to("cuda").contiguous()
+        y = torch.zeros_like(x)
+        for _ in range(args.applies):
+            P.apply_A(x, y)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": args.profile_case, "workload": f"lens2d_n{n}", "applies": args.applies,
+                          "device_gb": torch.cuda.max_memory_allocated() / 1e9}))
+        return
     name = {"qa64": "n64_bumps8", "a128": "n128_bumps32_rhs8", "a256": "n256_bumps32"}[args.profile_case]
     wl = si.workload(name)
     n = wl["n"]

@@ -6,9 +6,10 @@
 //     FP64 2-D FFTs, and one quadrant [3][L/2+1]^2 of each spectrum (G is even
 //     in both frequencies, G^1 odd in the first, G^2 odd in the second);
 //   * the apply A x in three passes, each a register-resident Stockham line FFT
-//     (fft_reg.cuh): rows forward (pad, contrast weights [m x^1, m x^2, p.x]),
-//     columns (forward, Fourier-side product y^d = k^2 Ghat w^d + G^d hat w^3,
-//     inverse), rows inverse (crop, + x);
+//     (fft_reg.cuh): the n nonzero columns forward (pad, contrast weights
+//     [m x^1, m x^2, p.x]), the L rows (forward, Fourier-side product
+//     y^d = k^2 Ghat w^d + G^d hat w^3, inverse, crop to n), the n columns
+//     inverse (crop, + x);
 //   * Q and S on the 9-point pattern; the stencils of the nine point classes by
 //     an FP64 Gram matrix M M^H summed over each class's complement and a
 //     Jacobi eigen-decomposition; S factored by the nested-dissection LU of
@@ -16,6 +17,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <complex>
 #include <vector>
 
@@ -170,92 +172,42 @@ __device__ __forceinline__ int pad8(int pos) { return pos + (pos >> 3); }
 
 template <int L> struct Geo2 {
     static constexpr int T = L / 8;
-    static constexpr int LS = L + L / 8;            // padded line stride
-    static constexpr int RB = T >= 256 ? 1 : 256 / T; // lines per block of the row passes
-};
-template <typename R, int L> struct ColGeo {
-    static constexpr int T = L / 8;
-    static constexpr int lim0 = (sizeof(R) == 4 ? 512 : 256) / T;
-    static constexpr int lim1 = lim0 > 16 ? 16 : (lim0 < 1 ? 1 : lim0);
-    static constexpr int COLS = lim1 > L ? L : lim1; // divides L (powers of two)
+    static constexpr int LS = L + L / 8; // padded line stride
 };
 
-// Pass 1, one row i2 < n per line: w = [m x^1, m x^2, p.x] padded to L, FFT
-// along x1.  W[b][f][i2][v1].
+// Pass 1, one column i1 < n per line, COLS adjacent columns per block: the
+// weights w = [m x^1, m x^2, p.x] of the block's columns staged in shared
+// memory (coalesced across columns), FFT along x2 (input rows >= n are the
+// zero padding), the L frequencies back through shared memory to W[b][f][v2][i1]
+// (rows of length n, coalesced across columns).
 template <typename R, int L>
-__global__ void __launch_bounds__(256) k2d_rowfwd(const typename cplx_of<R>::type *__restrict__ x,
-                                                  const typename cplx_of<R>::type *__restrict__ m,
-                                                  const typename cplx_of<R>::type *__restrict__ p,
-                                                  typename cplx_of<R>::type *__restrict__ W, int n,
-                                                  const typename cplx_of<R>::type *__restrict__ tw)
+__global__ void __launch_bounds__(1024)
+    k2d_colfwd(const typename cplx_of<R>::type *__restrict__ x, const typename cplx_of<R>::type *__restrict__ m,
+               const typename cplx_of<R>::type *__restrict__ p, typename cplx_of<R>::type *__restrict__ W, int n,
+               const typename cplx_of<R>::type *__restrict__ tw, int COLS)
 {
     using C = typename cplx_of<R>::type;
-    using G = Geo2<L>;
-    constexpr int T = G::T;
-    extern __shared__ unsigned char smem_raw[];
-    C *sm = reinterpret_cast<C *>(smem_raw);
-    const int line = threadIdx.x / T, t = threadIdx.x % T;
-    const int row = blockIdx.x * G::RB + line;
-    const bool ok = row < n;
-    const long b = blockIdx.y, N = (long)n * n;
-    const C *xb = x + b * 2 * N;
-    C *lb = sm + line * G::LS;
-    auto buf = [&](int pos) -> C & { return lb[pad8(pos)]; };
-    auto sync = [&]() { if (T <= 32) __syncwarp(); else __syncthreads(); };
-#pragma unroll 1
-    for (int f = 0; f < 3; ++f) {
-        C v[8];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int i1 = t + T * q;
-            C w = czero<C>();
-            if (ok && i1 < n) {
-                const long o = (long)row * n + i1;
-                if (f < 2) w = cmul(m[o], xb[f * N + o]);
-                else w = cfma(p[o], xb[o], cmul(p[N + o], xb[N + o]));
-            }
-            v[q] = w;
-            v[q + 4] = czero<C>();
-        }
-        fftr::fft_line<-1, L, true>(v, t, buf, sync, tw);
-        if (ok) {
-            C *dst = W + ((b * 3 + f) * n + row) * (long)L;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) dst[t + T * q] = v[q];
-        }
-    }
-}
-
-// Pass 2, one column v1 per line, COLS adjacent columns per block: FFT along
-// x2 of the three fields, y^d = (k^2 Ghat) w^d + (G^d hat) w^3 (spectra with
-// 1/L^2 folded in), inverse FFT along x2, rows < n back into fields 0, 1 of W.
-template <typename R, int L>
-__global__ void __launch_bounds__(ColGeo<R, L>::COLS * (L / 8))
-    k2d_colprod(typename cplx_of<R>::type *W, const typename cplx_of<R>::type *__restrict__ spec, int n,
-                const typename cplx_of<R>::type *__restrict__ tw)
-{
-    using C = typename cplx_of<R>::type;
-    constexpr int T = L / 8, LS = L + L / 8, COLS = ColGeo<R, L>::COLS, H = L / 2 + 1;
+    constexpr int T = L / 8, LS = L + L / 8;
     extern __shared__ unsigned char smem_raw[];
     C *sm = reinterpret_cast<C *>(smem_raw);
     const int c = threadIdx.x / T, t = threadIdx.x % T;
-    const int col0 = blockIdx.x * COLS, v1 = col0 + c;
-    const long b = blockIdx.y;
-    C *Wb = W + b * 3 * (long)n * L;
+    const int col0 = blockIdx.x * COLS;
+    const long b = blockIdx.y, N = (long)n * n;
+    const C *xb = x + b * 2 * N;
     C *lb = sm + c * LS;
     auto buf = [&](int pos) -> C & { return lb[pad8(pos)]; };
     auto sync = [&]() { __syncthreads(); };
-    const int a1 = v1 <= L / 2 ? v1 : L - v1;
-    const R s1 = v1 > L / 2 ? (R)-1 : (R)1;
-    const C *K0 = spec, *K1 = spec + (long)H * H, *K2 = spec + 2 * (long)H * H;
-    C w3[8];
 #pragma unroll 1
-    for (int fi = 0; fi < 3; ++fi) {
-        const int f = fi == 0 ? 2 : fi - 1; // the p.x field first, kept in registers
-        // stage rows i2 < n of this block's columns (coalesced across columns)
+    for (int f = 0; f < 3; ++f) {
         for (int i = threadIdx.x; i < COLS * n; i += blockDim.x) {
-            const int cc = i % COLS, r = i / COLS;
-            sm[cc * LS + pad8(r)] = Wb[((long)f * n + r) * L + col0 + cc];
+            const int cc = i % COLS, r = i / COLS, i1 = col0 + cc;
+            C w = czero<C>();
+            if (i1 < n) {
+                const long o = (long)r * n + i1;
+                if (f < 2) w = cmul(m[o], xb[f * N + o]);
+                else w = cfma(p[o], xb[o], cmul(p[N + o], xb[N + o]));
+            }
+            sm[cc * LS + pad8(r)] = w;
         }
         __syncthreads();
         C v[8];
@@ -267,70 +219,122 @@ __global__ void __launch_bounds__(ColGeo<R, L>::COLS * (L / 8))
         }
         __syncthreads();
         fftr::fft_line<-1, L, true>(v, t, buf, sync, tw);
-        if (f == 2) {
-#pragma unroll
-            for (int q = 0; q < 8; ++q) w3[q] = v[q];
-            continue;
-        }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int v2 = t + T * q;
-            const int a2 = v2 <= L / 2 ? v2 : L - v2;
-            const long o = (long)a2 * H + a1;
-            C kd;
-            if (f == 0) kd = cscale(K1[o], s1);
-            else kd = cscale(K2[o], v2 > L / 2 ? (R)-1 : (R)1);
-            v[q] = cfma(K0[o], v[q], cmul(kd, w3[q]));
-        }
-        fftr::fft_line<1, L, false>(v, t, buf, sync, tw);
 #pragma unroll
         for (int q = 0; q < 8; ++q) buf(t + T * q) = v[q];
         __syncthreads();
-        for (int i = threadIdx.x; i < COLS * n; i += blockDim.x) {
-            const int cc = i % COLS, r = i / COLS;
-            Wb[((long)f * n + r) * L + col0 + cc] = sm[cc * LS + pad8(r)];
+        C *Wf = W + (b * 3 + f) * (long)L * n;
+        for (int i = threadIdx.x; i < COLS * L; i += blockDim.x) {
+            const int cc = i % COLS, r = i / COLS, i1 = col0 + cc;
+            if (i1 < n) Wf[(long)r * n + i1] = sm[cc * LS + pad8(r)];
         }
         __syncthreads();
     }
 }
 
-// Pass 3, one row i2 < n per line: inverse FFT along x1 of fields 0, 1,
-// y = x + (first n entries).
+// Pass 2, one row v2 (an x2 frequency) per line: the three fields' rows (length
+// n, zero-padded to L) transformed along x1 together, the Fourier-side product
+// y^d = (k^2 Ghat) w^d + (G^d hat) w^3 (spectra with 1/L^2 folded in; the
+// quadrant tables are read along a row, so the loads coalesce), the two results
+// transformed back, their first n entries written over fields 0, 1 of the row.
 template <typename R, int L>
-__global__ void __launch_bounds__(256) k2d_rowinv(const typename cplx_of<R>::type *__restrict__ W,
-                                                  const typename cplx_of<R>::type *__restrict__ x,
-                                                  typename cplx_of<R>::type *__restrict__ y, int n,
-                                                  const typename cplx_of<R>::type *__restrict__ tw)
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k2d_rowprod(typename cplx_of<R>::type *W,
+                                                   const typename cplx_of<R>::type *__restrict__ spec, int n,
+                                                   const typename cplx_of<R>::type *__restrict__ tw, int RB)
 {
     using C = typename cplx_of<R>::type;
     using G = Geo2<L>;
-    constexpr int T = G::T;
+    constexpr int T = G::T, H = L / 2 + 1;
     extern __shared__ unsigned char smem_raw[];
     C *sm = reinterpret_cast<C *>(smem_raw);
     const int line = threadIdx.x / T, t = threadIdx.x % T;
-    const int row = blockIdx.x * G::RB + line;
-    const bool ok = row < n;
+    const int v2 = blockIdx.x * RB + line; // L rows: RB divides L
+    const long b = blockIdx.y;
+    C *lb = sm + line * 3 * G::LS;
+    auto buf = [&](int k, int pos) -> C & { return lb[k * G::LS + pad8(pos)]; };
+    // a line within one warp of a block of whole warps needs only a warp barrier
+    const bool warp_lines = T <= 32 && (blockDim.x & 31) == 0;
+    auto sync = [&]() { if (warp_lines) __syncwarp(); else __syncthreads(); };
+    C *Wr = W + b * 3 * (long)L * n + (long)v2 * n;
+    const long fs = (long)L * n; // field stride
+    C v[3][8];
+#pragma unroll
+    for (int f = 0; f < 3; ++f)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i1 = t + T * q;
+            v[f][q] = i1 < n ? Wr[f * fs + i1] : czero<C>();
+            v[f][q + 4] = czero<C>();
+        }
+    fftr::fft_lines<-1, L, true, 3>(v, t, buf, sync, tw);
+    const int a2 = v2 <= L / 2 ? v2 : L - v2;
+    const R s2 = v2 > L / 2 ? (R)-1 : (R)1;
+    const C *K0 = spec + (long)a2 * H, *K1 = K0 + (long)H * H, *K2 = K1 + (long)H * H;
+    C y[2][8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int v1 = t + T * q;
+        const int a1 = v1 <= L / 2 ? v1 : L - v1;
+        const R s1 = v1 > L / 2 ? (R)-1 : (R)1;
+        const C k0 = K0[a1], k1 = cscale(K1[a1], s1), k2 = cscale(K2[a1], s2);
+        y[0][q] = cfma(k0, v[0][q], cmul(k1, v[2][q]));
+        y[1][q] = cfma(k0, v[1][q], cmul(k2, v[2][q]));
+    }
+    fftr::fft_lines<1, L, false, 2>(y, t, buf, sync, tw);
+#pragma unroll
+    for (int f = 0; f < 2; ++f)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i1 = t + T * q;
+            if (i1 < n) Wr[f * fs + i1] = y[f][q];
+        }
+}
+
+// Pass 3, one column i1 < n per line, COLS adjacent columns per block: the
+// L rows of fields 0, 1 staged in shared memory (coalesced across columns),
+// inverse FFT along x2, rows i2 < n back through shared memory, y = x + result.
+template <typename R, int L>
+__global__ void __launch_bounds__(1024)
+    k2d_colinv(const typename cplx_of<R>::type *__restrict__ W, const typename cplx_of<R>::type *__restrict__ x,
+               typename cplx_of<R>::type *__restrict__ y, int n, const typename cplx_of<R>::type *__restrict__ tw,
+               int COLS)
+{
+    using C = typename cplx_of<R>::type;
+    constexpr int T = L / 8, LS = L + L / 8;
+    extern __shared__ unsigned char smem_raw[];
+    C *sm = reinterpret_cast<C *>(smem_raw);
+    const int c = threadIdx.x / T, t = threadIdx.x % T;
+    const int col0 = blockIdx.x * COLS;
     const long b = blockIdx.y, N = (long)n * n;
-    C *lb = sm + line * G::LS;
+    C *lb = sm + c * LS;
     auto buf = [&](int pos) -> C & { return lb[pad8(pos)]; };
-    auto sync = [&]() { if (T <= 32) __syncwarp(); else __syncthreads(); };
+    auto sync = [&]() { __syncthreads(); };
 #pragma unroll 1
     for (int f = 0; f < 2; ++f) {
+        const C *Wf = W + (b * 3 + f) * (long)L * n;
+        for (int i = threadIdx.x; i < COLS * L; i += blockDim.x) {
+            const int cc = i % COLS, r = i / COLS, i1 = col0 + cc;
+            sm[cc * LS + pad8(r)] = i1 < n ? Wf[(long)r * n + i1] : czero<C>();
+        }
+        __syncthreads();
         C v[8];
-        const C *src = W + ((b * 3 + f) * n + (ok ? row : 0)) * (long)L;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) v[q] = ok ? src[t + T * q] : czero<C>();
+        for (int q = 0; q < 8; ++q) v[q] = buf(t + T * q);
+        __syncthreads();
         fftr::fft_line<1, L, false>(v, t, buf, sync, tw);
-        if (ok) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int i1 = t + T * q;
-                if (i1 < n) {
-                    const long o = (b * 2 + f) * N + (long)row * n + i1;
-                    y[o] = x[o] + v[q];
-                }
+        for (int q = 0; q < 4; ++q) {
+            const int r = t + T * q;
+            if (r < n) buf(r) = v[q];
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < COLS * n; i += blockDim.x) {
+            const int cc = i % COLS, r = i / COLS, i1 = col0 + cc;
+            if (i1 < n) {
+                const long o = (b * 2 + f) * N + (long)r * n + i1;
+                y[o] = x[o] + sm[cc * LS + pad8(r)];
             }
         }
+        __syncthreads();
     }
 }
 
@@ -351,24 +355,29 @@ spm_status apply_L(spm2_problem_s *P, const void *xv, void *yv, int nrhs, cudaSt
     const C *p = dbl ? P->p128.as<C>() : P->p64.as<C>();
     const C *spec = dbl ? P->spec128.as<C>() : P->spec64.as<C>();
     const C *tw = dbl ? P->tw128.as<C>() : P->tw64.as<C>();
-    const long per = 3L * n * L; // workspace elements per right-hand side
+    const long per = 3L * n * L; // workspace elements per right-hand side: W[3][L][n]
     int chunk = (int)std::max<long>(1, std::min<long>(nrhs, (512L << 20) / (long)(per * sizeof(C))));
     SPM_TRY(P->work.ensure(sizeof(C) * per * chunk));
     C *W = P->work.as<C>();
     using G = Geo2<L>;
-    using CG = ColGeo<R, L>;
-    const size_t sm_rows = sizeof(C) * G::RB * G::LS, sm_cols = sizeof(C) * CG::COLS * G::LS;
-    SPM_TRY(allow_smem(k2d_rowfwd<R, L>, sm_rows));
-    SPM_TRY(allow_smem(k2d_rowinv<R, L>, sm_rows));
-    SPM_TRY(allow_smem(k2d_colprod<R, L>, sm_cols));
+    // Columns per block of the column passes and rows per block of the row pass:
+    // as many as keep two blocks per SM busy (powers of two, at most 16
+    // columns and 1024 threads, at most 256 threads per row block).
+    auto pow2_floor = [](long v) { int r = 1; while ((long)r * 2 <= v) r *= 2; return r; };
+    const int cols = std::max(1, std::min({16, 1024 / G::T, pow2_floor(std::max(1L, (long)n / 304))}));
+    const int rb = std::max(1, std::min({L, std::max(1, 256 / G::T), pow2_floor(std::max(1L, (long)L / 304))}));
+    const size_t sm_rows = sizeof(C) * rb * 3 * G::LS, sm_cols = sizeof(C) * cols * G::LS;
+    SPM_TRY(allow_smem(k2d_colfwd<R, L>, sm_cols));
+    SPM_TRY(allow_smem(k2d_rowprod<R, L>, sm_rows));
+    SPM_TRY(allow_smem(k2d_colinv<R, L>, sm_cols));
     for (int b0 = 0; b0 < nrhs; b0 += chunk) {
         const int nb_ = std::min(chunk, nrhs - b0);
         const C *x = reinterpret_cast<const C *>(xv) + (long)b0 * 2 * N;
         C *y = reinterpret_cast<C *>(yv) + (long)b0 * 2 * N;
-        const dim3 grow((unsigned)((n + G::RB - 1) / G::RB), (unsigned)nb_);
-        k2d_rowfwd<R, L><<<grow, G::RB * G::T, sm_rows, s>>>(x, m, p, W, n, tw);
-        k2d_colprod<R, L><<<dim3(L / CG::COLS, (unsigned)nb_), CG::COLS * G::T, sm_cols, s>>>(W, spec, n, tw);
-        k2d_rowinv<R, L><<<grow, G::RB * G::T, sm_rows, s>>>(W, x, y, n, tw);
+        const dim3 gcol((unsigned)((n + cols - 1) / cols), (unsigned)nb_);
+        k2d_colfwd<R, L><<<gcol, cols * G::T, sm_cols, s>>>(x, m, p, W, n, tw, cols);
+        k2d_rowprod<R, L><<<dim3(L / rb, (unsigned)nb_), rb * G::T, sm_rows, s>>>(W, spec, n, tw, rb);
+        k2d_colinv<R, L><<<gcol, cols * G::T, sm_cols, s>>>(W, x, y, n, tw, cols);
     }
     SPM_CUDA_TRY(cudaGetLastError());
     return SPM_OK;
@@ -505,52 +514,66 @@ Geom2 geom2(int cls, int n)
     return g;
 }
 
-constexpr int GRAM_CHUNKS = 16;
+constexpr int GRAM_BLOCKS = 608; // 4 x 152 SMs
+constexpr int GRAM_UT = 64;      // complement offsets staged per tile
 
-// Partial Gram sums over a slice of the complement box, one block per
-// (pair (o, o'), slice): kinds 0..3 = C_00, C_11, C_12, C_22 with
-// C_ab[o][o'] = sum_u K_a(o - u) conj(K_b(o' - u)), K_0 = G, K_d = G^d.
-__global__ void __launch_bounds__(256) k2_gram(const double2 *__restrict__ E, Geom2 g, int n, double2 *part)
+// Partial Gram sums, one block per slice of the complement box: the block
+// stages, for a tile of complement offsets u, the entries K_q(o - u) of the
+// three kernels at the class's T neighbourhood offsets o (shared memory), and
+// thread (o, o') accumulates the four sums C_00, C_11, C_12, C_22 of
+// C_ab[o][o'] = sum_u K_a(o - u) conj(K_b(o' - u)), K_0 = G, K_d = G^d, over
+// the tile (u in the neighbourhood box itself is skipped).  part[block][kind][pair].
+__global__ void __launch_bounds__(128) k2_gram(const double2 *__restrict__ E, Geom2 g, int n, double2 *part)
 {
-    const int pair = blockIdx.x, chunk = blockIdx.y;
-    const int o = pair / g.T, op = pair % g.T;
+    __shared__ double2 st[GRAM_UT][9][3];
     const int W = 2 * n - 1;
     const long W2 = (long)W * W;
     const int w1 = g.rhi[0] - g.rlo[0] + 1, w2 = g.rhi[1] - g.rlo[1] + 1;
     const long box = (long)w1 * w2;
-    const long per = (box + GRAM_CHUNKS - 1) / GRAM_CHUNKS;
-    const long u0 = chunk * per, u1 = min(box, u0 + per);
+    const long per = (box + gridDim.x - 1) / gridDim.x;
+    const long u0 = (long)blockIdx.x * per, u1 = min(box, u0 + per);
+    const int T = g.T, pair = threadIdx.x;
+    const bool act = pair < T * T;
+    const int o = act ? pair / T : 0, op = act ? pair % T : 0;
+    int tlo[2] = {g.off[0][0], g.off[0][1]}, thi[2] = {g.off[T - 1][0], g.off[T - 1][1]};
     double2 acc[4] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
-    for (long idx = u0 + threadIdx.x; idx < u1; idx += blockDim.x) {
-        const int u1c = g.rlo[0] + (int)(idx % w1), u2c = g.rlo[1] + (int)(idx / w1);
-        bool in_tau = false;
-        for (int q = 0; q < g.T; ++q) in_tau |= (g.off[q][0] == u1c && g.off[q][1] == u2c);
-        if (in_tau) continue;
-        const long ea = (long)(g.off[o][1] - u2c + n - 1) * W + (g.off[o][0] - u1c + n - 1);
-        const long eb = (long)(g.off[op][1] - u2c + n - 1) * W + (g.off[op][0] - u1c + n - 1);
-        const double2 a0 = E[ea], a1 = E[W2 + ea], a2 = E[2 * W2 + ea];
-        const double2 b0 = E[eb], b1 = E[W2 + eb], b2 = E[2 * W2 + eb];
-        acc[0] = cfma(a0, conj_of(b0), acc[0]);
-        acc[1] = cfma(a1, conj_of(b1), acc[1]);
-        acc[2] = cfma(a1, conj_of(b2), acc[2]);
-        acc[3] = cfma(a2, conj_of(b2), acc[3]);
-    }
-    __shared__ double2 red[4][8];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int kk = 0; kk < 4; ++kk) {
-        double x = acc[kk].x, y = acc[kk].y;
-        for (int off = 16; off > 0; off >>= 1) {
-            x += __shfl_down_sync(0xffffffffu, x, off);
-            y += __shfl_down_sync(0xffffffffu, y, off);
+    for (long t0 = u0; t0 < u1; t0 += GRAM_UT) {
+        const int cnt = (int)min((long)GRAM_UT, u1 - t0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < cnt * T * 3; i += blockDim.x) {
+            const int ul = i / (T * 3), rem = i % (T * 3), oo = rem / 3, q = rem % 3;
+            const long idx = t0 + ul;
+            const int uu1 = g.rlo[0] + (int)(idx % w1), uu2 = g.rlo[1] + (int)(idx / w1);
+            const long e = (long)(g.off[oo][1] - uu2 + n - 1) * W + (g.off[oo][0] - uu1 + n - 1);
+            st[ul][oo][q] = E[q * W2 + e];
         }
-        if (lane == 0) red[kk][wid] = make_double2(x, y);
+        __syncthreads();
+        if (act) {
+            for (int ul = 0; ul < cnt; ++ul) {
+                const long idx = t0 + ul;
+                const int uu1 = g.rlo[0] + (int)(idx % w1), uu2 = g.rlo[1] + (int)(idx / w1);
+                if (uu1 >= tlo[0] && uu1 <= thi[0] && uu2 >= tlo[1] && uu2 <= thi[1]) continue; // u in tau
+                const double2 a0 = st[ul][o][0], a1 = st[ul][o][1], a2 = st[ul][o][2];
+                const double2 b0 = st[ul][op][0], b1 = st[ul][op][1], b2 = st[ul][op][2];
+                acc[0] = cfma(a0, conj_of(b0), acc[0]);
+                acc[1] = cfma(a1, conj_of(b1), acc[1]);
+                acc[2] = cfma(a1, conj_of(b2), acc[2]);
+                acc[3] = cfma(a2, conj_of(b2), acc[3]);
+            }
+        }
     }
-    __syncthreads();
-    if (threadIdx.x < 4) {
-        double2 s = make_double2(0, 0);
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s = s + red[threadIdx.x][w];
-        part[((long)chunk * 4 + threadIdx.x) * 81 + pair] = s;
-    }
+    if (act)
+        for (int kk = 0; kk < 4; ++kk) part[((long)blockIdx.x * 4 + kk) * 81 + pair] = acc[kk];
+}
+
+// sum the per-block partial Gram sums: out[kind][pair]
+__global__ void k2_gram_sum(const double2 *__restrict__ part, int nblocks, double2 *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 4 * 81) return;
+    double2 s = make_double2(0, 0);
+    for (int b = 0; b < nblocks; ++b) s = s + part[(long)b * 4 * 81 + i];
+    out[i] = s;
 }
 
 __device__ __forceinline__ double2 zm(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
@@ -566,11 +589,7 @@ __global__ void k2_eig(const double2 *__restrict__ part, const double2 *__restri
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     const int T = g.T, M = 2 * T;
     for (int kk = 0; kk < 4; ++kk)
-        for (int pr = 0; pr < T * T; ++pr) {
-            double2 s = make_double2(0, 0);
-            for (int c = 0; c < GRAM_CHUNKS; ++c) s = s + part[((long)c * 4 + kk) * 81 + pr];
-            Cs[kk][pr] = s;
-        }
+        for (int pr = 0; pr < T * T; ++pr) Cs[kk][pr] = part[kk * 81 + pr];
     const double k4 = k * k * k * k;
     for (int r = 0; r < M; ++r)
         for (int c = 0; c < M; ++c) {
@@ -776,15 +795,17 @@ spm_status fit_stencils(spm2_problem_s *P)
     const int n = P->n;
     cudaStream_t s = P->stream;
     DevBuf part, out;
-    SPM_TRY(part.ensure(sizeof(double2) * GRAM_CHUNKS * 4 * 81));
+    SPM_TRY(part.ensure(sizeof(double2) * (GRAM_BLOCKS + 1) * 4 * 81));
+    double2 *sums = part.as<double2>() + (long)GRAM_BLOCKS * 4 * 81;
     SPM_TRY(out.ensure(sizeof(double2) * 9 * (18 + 27) * 2 + sizeof(double) * 9 * 18));
     double2 *al = out.as<double2>(), *be = al + 9 * 18 * 2;
     double *sv = reinterpret_cast<double *>(be + 9 * 27 * 2);
     for (int cls = 0; cls < 9; ++cls) {
         const Geom2 g = geom2(cls, n);
-        k2_gram<<<dim3(g.T * g.T, GRAM_CHUNKS), 256, 0, s>>>(P->entries.as<double2>(), g, n, part.as<double2>());
-        k2_eig<<<1, 32, 0, s>>>(part.as<double2>(), P->entries.as<double2>(), g, n, P->k, al + cls * 36,
-                                be + cls * 54, sv + cls * 18);
+        k2_gram<<<GRAM_BLOCKS, 128, 0, s>>>(P->entries.as<double2>(), g, n, part.as<double2>());
+        k2_gram_sum<<<3, 128, 0, s>>>(part.as<double2>(), GRAM_BLOCKS, sums);
+        k2_eig<<<1, 32, 0, s>>>(sums, P->entries.as<double2>(), g, n, P->k, al + cls * 36, be + cls * 54,
+                                sv + cls * 18);
         SPM_CUDA_TRY(cudaGetLastError());
     }
     P->alpha_h.resize(9 * 18 * 2 * 2);
