@@ -88,6 +88,182 @@ __global__ void k_front_assemble(C *F, int f, const C *__restrict__ S, const int
     }
 }
 
+// ---- batched small fronts: one block per front, the whole front in shared memory
+// A front of f unknowns (o3 own first) is assembled from S and the children's
+// updates, then swept by Gauss-Jordan over its o3 own pivots with partial
+// pivoting among the own rows (explicit row swaps) and the static pivot floor:
+// after the sweep the front holds [(P F11)^-1, F11^-1 F12; -F21 (P F11)^-1,
+// F22 - F21 F11^-1 F12], from which G = [F11^-1; F21 F11^-1] (columns put back
+// in place), X = F11^-1 F12 and the update F22 - F21 X are written out.  The
+// same quantities as the per-front path (dense inverse + GEMMs), in one launch
+// for every small front of a tree level.
+struct BatchFront {
+    int own_off, nown, map_off, e0, e1, e2, ew0, ew1, f, o3, nch;
+    int ch_bc[2], ch_rel[2];
+    long fac_off;
+    void *upd;
+    const void *ch_upd[2];
+};
+
+template <typename C> __device__ __forceinline__ C bdiv(C a, C b)
+{
+    using R = decltype(a.x);
+    const R d = b.x * b.x + b.y * b.y;
+    C r;
+    r.x = (a.x * b.x + a.y * b.y) / d;
+    r.y = (a.y * b.x - a.x * b.y) / d;
+    return r;
+}
+
+template <typename C>
+__global__ void __launch_bounds__(256) k_front_batch(const BatchFront *__restrict__ fronts, const C *__restrict__ S,
+                                                     const int *__restrict__ pts, const int *__restrict__ maps,
+                                                     const int *__restrict__ rels, GridDesc g, C *fac, double tau,
+                                                     int *raised)
+{
+    using R = decltype(C{}.x);
+    extern __shared__ unsigned char smem_raw[];
+    const BatchFront fr = fronts[blockIdx.x];
+    const int f = fr.f, o3 = fr.o3, b3 = f - o3;
+    C *F = reinterpret_cast<C *>(smem_raw); // f x f, column-major: row r, column c at c * f + r
+    C *prow = F + (long)f * f;              // the scaled pivot row
+    C *pcol = prow + f;                     // the pivot column before the step
+    int *perm = reinterpret_cast<int *>(pcol + f);
+    __shared__ R red_v[8];
+    __shared__ int red_i[8];
+    __shared__ R s_floor;
+    __shared__ int s_p;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
+    for (int i = tid; i < f * f; i += nt) F[i] = czero<C>();
+    for (int i = tid; i < o3; i += nt) perm[i] = i;
+    __syncthreads();
+    const int D = g.D, DD = g.D * g.D;
+    const int *own_pts = pts + fr.own_off, *lmap = maps + fr.map_off;
+    for (int gid = tid; gid < fr.nown * g.nsten; gid += nt) {
+        const int a = gid / g.nsten, s = gid % g.nsten;
+        const int o1 = s % 3 - 1, o2 = (s / 3) % 3 - 1, oz = g.nsten == 27 ? s / 9 - 1 : 0;
+        const int i = own_pts[a];
+        const int i1 = i % g.n1, i2 = (i / g.n1) % g.n2, i3 = i / (g.n1 * g.n2);
+        const int j1 = i1 + o1, j2 = i2 + o2, j3 = i3 + oz;
+        if (j1 < 0 || j2 < 0 || j3 < 0 || j1 >= g.n1 || j2 >= g.n2 || j3 >= g.n3) continue;
+        const int lj = lmap[((j3 - fr.e2) * fr.ew1 + (j2 - fr.e1)) * fr.ew0 + (j1 - fr.e0)];
+        if (lj < 0) continue;
+        const long j = ((long)j3 * g.n2 + j2) * g.n1 + j1;
+        const C *blk = S + ((long)i * g.nsten + s) * DD;
+        for (int c = 0; c < D; ++c)
+            for (int q = 0; q < D; ++q) F[(long)(D * lj + q) * f + D * a + c] = blk[c * D + q];
+        if (lj >= fr.nown) {
+            const C *bj = S + (j * g.nsten + (g.nsten - 1 - s)) * DD;
+            for (int c = 0; c < D; ++c)
+                for (int q = 0; q < D; ++q) F[(long)(D * a + q) * f + D * lj + c] = bj[c * D + q];
+        }
+    }
+    __syncthreads();
+    for (int ch = 0; ch < fr.nch; ++ch) { // children one after the other: their maps overlap
+        const C *U = reinterpret_cast<const C *>(fr.ch_upd[ch]);
+        const int bc = fr.ch_bc[ch];
+        const int *rel = rels + fr.ch_rel[ch];
+        for (int e = tid; e < bc * bc; e += nt) {
+            const C u = U[e];
+            C &d = F[(long)rel[e / bc] * f + rel[e % bc]];
+            d.x += u.x;
+            d.y += u.y;
+        }
+        __syncthreads();
+    }
+    // pivot floor: tau times the largest |entry| of F11
+    R mx = 0;
+    for (int e = tid; e < o3 * o3; e += nt) {
+        const C a = F[(long)(e / o3) * f + e % o3];
+        mx = max(mx, a.x * a.x + a.y * a.y);
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) red_v[wid] = mx;
+    __syncthreads();
+    if (tid == 0) {
+        R m2 = red_v[0];
+        for (int w = 1; w < nt / 32; ++w) m2 = max(m2, red_v[w]);
+        s_floor = (R)(tau * sqrt((double)m2));
+    }
+    __syncthreads();
+    const R fl = s_floor;
+    C one;
+    one.x = 1;
+    one.y = 0;
+    for (int k = 0; k < o3; ++k) {
+        if (wid == 0) { // the largest |F[i][k]| over the unpivoted own rows, lowest row on ties
+            R best = -1;
+            int bi = -1;
+            for (int i = k + lane; i < o3; i += 32) {
+                const C a = F[(long)k * f + i];
+                const R v = a.x * a.x + a.y * a.y;
+                if (v > best) { best = v; bi = i; }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const R ov = __shfl_xor_sync(0xffffffffu, best, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+                if (ov > best || (ov == best && oi >= 0 && (bi < 0 || oi < bi))) { best = ov; bi = oi; }
+            }
+            if (lane == 0) s_p = bi;
+        }
+        __syncthreads();
+        const int p = s_p;
+        if (p != k) {
+            for (int c = tid; c < f; c += nt) {
+                const C t = F[(long)c * f + p];
+                F[(long)c * f + p] = F[(long)c * f + k];
+                F[(long)c * f + k] = t;
+            }
+            if (tid == 0) { const int t = perm[p]; perm[p] = perm[k]; perm[k] = t; }
+            __syncthreads();
+        }
+        C d = F[(long)k * f + k];
+        const R ad2 = d.x * d.x + d.y * d.y;
+        if (ad2 < fl * fl) { // the static pivot floor
+            const R ad = sqrt(ad2);
+            const R sx = ad > 0 ? d.x / ad : (R)1, sy = ad > 0 ? d.y / ad : (R)0;
+            d.x = fl * sx;
+            d.y = fl * sy;
+            if (tid == 0) atomicAdd(raised, 1);
+        }
+        const C inv_d = bdiv(one, d);
+        for (int j = tid; j < f; j += nt) {
+            prow[j] = j == k ? inv_d : cmul(F[(long)j * f + k], inv_d);
+            pcol[j] = F[(long)k * f + j];
+        }
+        __syncthreads();
+        for (int e = tid; e < f * f; e += nt) {
+            const int i = e % f, j = e / f;
+            C v;
+            if (i == k) {
+                v = prow[j];
+            } else if (j == k) {
+                v = cmul(pcol[i], inv_d);
+                v.x = -v.x;
+                v.y = -v.y;
+            } else {
+                v = F[e];
+                const C pc = pcol[i], pr = prow[j];
+                v.x -= pc.x * pr.x - pc.y * pr.y;
+                v.y -= pc.x * pr.y + pc.y * pr.x;
+            }
+            F[e] = v;
+        }
+        __syncthreads();
+    }
+    C *G = fac + fr.fac_off; // f x o3, ld f
+    for (int e = tid; e < f * o3; e += nt) {
+        const int r = e % f, j = e / f;
+        C v = F[(long)j * f + r];
+        if (r >= o3) { v.x = -v.x; v.y = -v.y; }
+        G[(long)perm[j] * f + r] = v;
+    }
+    C *X = G + (long)f * o3; // o3 x b3, ld o3
+    for (int e = tid; e < o3 * b3; e += nt) X[e] = F[(long)(o3 + e / o3) * f + e % o3];
+    C *U = reinterpret_cast<C *>(fr.upd); // b3 x b3, ld b3
+    for (int e = tid; e < b3 * b3; e += nt) U[e] = F[(long)(o3 + e / b3) * f + o3 + e % b3];
+}
+
 template <typename C>
 __global__ void k_extend_add(C *F, int f, const C *__restrict__ U, int bc, const int *__restrict__ rel)
 {
@@ -491,12 +667,24 @@ static spm_status factor_typed(const SparseSys &SY, NDFactor *F, bool half_store
     // its own front, update stack and dense workspace.  A subtree root's update
     // goes to a buffer of its own, where its parent (above the subtrees, factored
     // afterwards on the problem's stream) finds it.
+    // Small fronts (f <= BATCH_FMAX, whose whole subtree is small) are factored
+    // first, level by level, each level in one launch of k_front_batch; their
+    // updates go to buffers of their own.  The stream pool below handles the rest.
+    const int BATCH_FMAX = sizeof(R) == 8 ? 112 : 160;
+    std::vector<char> batched(NN, 0);
+    for (int id = 0; id < NN; ++id) { // postorder: children before parents
+        const Node &nd = nodes[id];
+        bool ok = !half_store && D * (nd.nown + nd.nbnd) <= BATCH_FMAX;
+        for (int ch : {nd.left, nd.right})
+            if (ch >= 0 && !batched[ch]) ok = false;
+        batched[id] = ok ? 1 : 0;
+    }
     const size_t one_block = sizeof(R) == 4 ? 768 : 384;
     std::vector<size_t> smax(NN, 0);
     std::vector<int> parent(NN, -1);
     for (int id = 0; id < NN; ++id) { // postorder: children before parents
         const Node &nd = nodes[id];
-        smax[id] = D * (size_t)nd.nown;
+        smax[id] = batched[id] ? 0 : D * (size_t)nd.nown;
         for (int ch : {nd.left, nd.right})
             if (ch >= 0) { smax[id] = std::max(smax[id], smax[ch]); parent[ch] = id; }
     }
@@ -505,7 +693,7 @@ static spm_status factor_typed(const SparseSys &SY, NDFactor *F, bool half_store
     const int NSTREAM = 16;
     int nsub = 0;
     for (int id = 0; id < NN; ++id)
-        if (smax[id] <= one_block && (parent[id] < 0 || smax[parent[id]] > one_block)) {
+        if (!batched[id] && smax[id] <= one_block && (parent[id] < 0 || smax[parent[id]] > one_block)) {
             sub_root[id] = 1;
             ++nsub;
         }
@@ -520,7 +708,8 @@ static spm_status factor_typed(const SparseSys &SY, NDFactor *F, bool half_store
                 else if (nd.right >= 0) first = nd.right;
                 else break;
             }
-            for (int j = first; j <= id; ++j) group[j] = k % NSTREAM;
+            for (int j = first; j <= id; ++j)
+                if (!batched[j]) group[j] = k % NSTREAM;
             ++k;
         }
     }
@@ -531,14 +720,21 @@ static spm_status factor_typed(const SparseSys &SY, NDFactor *F, bool half_store
     std::vector<size_t> g_front(ngroups, 1), g_stack(ngroups, 1), g_now(ngroups, 0), g_gx(ngroups, 1);
     std::vector<size_t> root_upd_off(NN, 0);
     size_t root_upd_total = 0;
+    std::vector<size_t> batch_upd_off(NN, 0);
+    size_t batch_upd_total = 0;
     for (int id = 0; id < NN; ++id) {
         const Node &nd = nodes[id];
+        if (batched[id]) {
+            batch_upd_off[id] = batch_upd_total;
+            batch_upd_total += upd_size[id];
+            continue;
+        }
         const size_t o3 = D * (size_t)nd.nown, b3 = D * (size_t)nd.nbnd, f = o3 + b3;
         const int g = slot(id);
         g_front[g] = std::max(g_front[g], f * f);
         g_gx[g] = std::max(g_gx[g], f * o3 + o3 * b3);
         for (int ch : {nd.left, nd.right})
-            if (ch >= 0 && !sub_root[ch]) g_now[g] -= upd_size[ch];
+            if (ch >= 0 && !sub_root[ch] && !batched[ch]) g_now[g] -= upd_size[ch];
         if (sub_root[id]) {
             root_upd_off[id] = root_upd_total;
             root_upd_total += upd_size[id];
@@ -562,6 +758,70 @@ static spm_status factor_typed(const SparseSys &SY, NDFactor *F, bool half_store
     if (half_store) SPM_TRY(F->scales.ensure(sizeof(float) * scale_total));
     SPM_TRY(F->info.ensure(sizeof(int) * 3)); // expired grid barrier, unused, raised pivots
     SPM_CUDA_TRY(cudaMemsetAsync(F->info.ptr, 0, sizeof(int) * 3, s));
+    const C *Sdev = reinterpret_cast<const C *>(sizeof(R) == 8 ? SY.S128 : SY.S64);
+    const int *dpts = F->pts.as<int>(), *dmaps = F->maps.as<int>(), *drels = F->rels.as<int>();
+    C *fac = F->fac.as<C>();
+    int *dinfo = F->info.as<int>();
+    std::vector<const C *> upd_ptr(NN, nullptr); // where each node's update sits
+    // the batched levels, deepest first, on the problem's stream
+    DevBuf batch_upd, batch_desc;
+    {
+        SPM_TRY(batch_upd.ensure(sizeof(C) * std::max<size_t>(batch_upd_total, 1)));
+        C *bu = batch_upd.as<C>();
+        int maxd = 0;
+        for (const Node &nd : nodes) maxd = std::max(maxd, nd.depth);
+        std::vector<std::vector<BatchFront>> lv(maxd + 1);
+        size_t nbf = 0;
+        for (int id = 0; id < NN; ++id) {
+            if (!batched[id]) continue;
+            const Node &nd = nodes[id];
+            upd_ptr[id] = bu + batch_upd_off[id];
+            BatchFront b;
+            b.own_off = (int)nd.own_off;
+            b.nown = nd.nown;
+            b.map_off = (int)nd.map_off;
+            b.e0 = nd.elo[0]; b.e1 = nd.elo[1]; b.e2 = nd.elo[2];
+            b.ew0 = nd.ehi[0] - nd.elo[0];
+            b.ew1 = nd.ehi[1] - nd.elo[1];
+            b.o3 = D * nd.nown;
+            b.f = b.o3 + D * nd.nbnd;
+            b.fac_off = nd.fac_off;
+            b.upd = bu + batch_upd_off[id];
+            b.nch = 0;
+            for (int ch : {nd.left, nd.right}) {
+                if (ch < 0 || nodes[ch].nbnd == 0) continue;
+                b.ch_bc[b.nch] = D * nodes[ch].nbnd;
+                b.ch_rel[b.nch] = (int)nodes[ch].rel_off;
+                b.ch_upd[b.nch] = upd_ptr[ch];
+                ++b.nch;
+            }
+            lv[nd.depth].push_back(b);
+            ++nbf;
+        }
+        if (nbf > 0) {
+            SPM_TRY(batch_desc.ensure(sizeof(BatchFront) * nbf));
+            std::vector<BatchFront> all;
+            std::vector<std::pair<size_t, size_t>> range(maxd + 1);
+            for (int d = maxd; d >= 0; --d) {
+                range[d] = {all.size(), lv[d].size()};
+                all.insert(all.end(), lv[d].begin(), lv[d].end());
+            }
+            SPM_CUDA_TRY(cudaMemcpy(batch_desc.ptr, all.data(), sizeof(BatchFront) * nbf, cudaMemcpyHostToDevice));
+            const size_t smem_max = sizeof(C) * ((size_t)BATCH_FMAX * BATCH_FMAX + 2 * BATCH_FMAX) + sizeof(int) * BATCH_FMAX;
+            SPM_CUDA_TRY(cudaFuncSetAttribute(k_front_batch<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+            const GridDesc gd2{n1, n2, n3d, D, SY.nsten};
+            for (int d = maxd; d >= 0; --d) {
+                if (range[d].second == 0) continue;
+                int fm = 1;
+                for (const BatchFront &b : lv[d]) fm = std::max(fm, b.f);
+                const size_t smem = sizeof(C) * ((size_t)fm * fm + 2 * fm) + sizeof(int) * fm;
+                k_front_batch<C><<<(unsigned)range[d].second, 256, smem, s>>>(
+                    batch_desc.as<BatchFront>() + range[d].first, Sdev, dpts, dmaps, drels, gd2, fac, pivot_floor<R>(),
+                    dinfo + 2);
+            }
+            SPM_CUDA_TRY(cudaGetLastError());
+        }
+    }
     // per-slot buffers and streams (slot ngroups - 1 is the problem's stream)
     struct Slot {
         DevBuf front, stack, gx;
@@ -597,11 +857,6 @@ static spm_status factor_typed(const SparseSys &SY, NDFactor *F, bool half_store
     }
     cudaEventDestroy(start_ev);
 
-    const C *Sdev = reinterpret_cast<const C *>(sizeof(R) == 8 ? SY.S128 : SY.S64);
-    const int *dpts = F->pts.as<int>(), *dmaps = F->maps.as<int>(), *drels = F->rels.as<int>();
-    C *fac = F->fac.as<C>();
-    int *dinfo = F->info.as<int>();
-    std::vector<const C *> upd_ptr(NN, nullptr); // where each node's update sits
     std::vector<size_t> top(ngroups, 0);
     auto factor_node = [&](int id) -> spm_status {
         Node &nd = nodes[id];
@@ -624,7 +879,7 @@ static spm_status factor_typed(const SparseSys &SY, NDFactor *F, bool half_store
             k_extend_add<C><<<blocks((long)bc * bc), 256, 0, ss>>>(front, f, upd_ptr[ch], bc, drels + c.rel_off);
         }
         for (int ch : {nd.left, nd.right})
-            if (ch >= 0 && !sub_root[ch]) top[g] -= upd_size[ch];
+            if (ch >= 0 && !sub_root[ch] && !batched[ch]) top[g] -= upd_size[ch];
         SPM_CUDA_TRY(cudaGetLastError());
         // F11^{-1} by Gauss-Jordan (partial pivoting inside the own block, static
         // pivot floor), then with G = [F11^{-1}; F21 F11^{-1}] (f x o3, ld f) and
@@ -667,7 +922,7 @@ static spm_status factor_typed(const SparseSys &SY, NDFactor *F, bool half_store
         SPM_CUDA_TRY(cudaStreamWaitEvent(s, slots[g].done, 0));
     }
     for (int id = 0; id < NN; ++id)
-        if (group[id] < 0) SPM_TRY(factor_node(id));
+        if (group[id] < 0 && !batched[id]) SPM_TRY(factor_node(id));
     int hinfo[3] = {0, 0, 0};
     SPM_CUDA_TRY(cudaMemcpyAsync(hinfo, dinfo, sizeof(int) * 3, cudaMemcpyDeviceToHost, s));
     SPM_CUDA_TRY(cudaStreamSynchronize(s));
