@@ -177,11 +177,12 @@ template <int L> struct Geo2 {
 
 // Pass 1, one column i1 < n per line, COLS adjacent columns per block: the
 // weights w = [m x^1, m x^2, p.x] of the block's columns staged in shared
-// memory (coalesced across columns), FFT along x2 (input rows >= n are the
-// zero padding), the L frequencies back through shared memory to W[b][f][v2][i1]
+// memory (coalesced across columns), the three fields transformed along x2
+// together (input rows >= n are the zero padding; the three lines share every
+// barrier), the L frequencies back through shared memory to W[b][f][v2][i1]
 // (rows of length n, coalesced across columns).
 template <typename R, int L>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256)
     k2d_colfwd(const typename cplx_of<R>::type *__restrict__ x, const typename cplx_of<R>::type *__restrict__ m,
                const typename cplx_of<R>::type *__restrict__ p, typename cplx_of<R>::type *__restrict__ W, int n,
                const typename cplx_of<R>::type *__restrict__ tw, int COLS)
@@ -189,45 +190,52 @@ __global__ void __launch_bounds__(1024)
     using C = typename cplx_of<R>::type;
     constexpr int T = L / 8, LS = L + L / 8;
     extern __shared__ unsigned char smem_raw[];
-    C *sm = reinterpret_cast<C *>(smem_raw);
+    C *sm = reinterpret_cast<C *>(smem_raw); // [field][column][LS]
     const int c = threadIdx.x / T, t = threadIdx.x % T;
     const int col0 = blockIdx.x * COLS;
     const long b = blockIdx.y, N = (long)n * n;
     const C *xb = x + b * 2 * N;
-    C *lb = sm + c * LS;
-    auto buf = [&](int pos) -> C & { return lb[pad8(pos)]; };
+    const long fsm = (long)COLS * LS;
+    auto buf = [&](int k, int pos) -> C & { return sm[k * fsm + c * LS + pad8(pos)]; };
     auto sync = [&]() { __syncthreads(); };
-#pragma unroll 1
-    for (int f = 0; f < 3; ++f) {
-        for (int i = threadIdx.x; i < COLS * n; i += blockDim.x) {
-            const int cc = i % COLS, r = i / COLS, i1 = col0 + cc;
-            C w = czero<C>();
-            if (i1 < n) {
-                const long o = (long)r * n + i1;
-                if (f < 2) w = cmul(m[o], xb[f * N + o]);
-                else w = cfma(p[o], xb[o], cmul(p[N + o], xb[N + o]));
-            }
-            sm[cc * LS + pad8(r)] = w;
+    for (int i = threadIdx.x; i < COLS * n; i += blockDim.x) {
+        const int cc = i % COLS, r = i / COLS, i1 = col0 + cc;
+        C w0 = czero<C>(), w1 = czero<C>(), w2 = czero<C>();
+        if (i1 < n) {
+            const long o = (long)r * n + i1;
+            const C mm = m[o], e0 = xb[o], e1 = xb[N + o];
+            w0 = cmul(mm, e0);
+            w1 = cmul(mm, e1);
+            w2 = cfma(p[o], e0, cmul(p[N + o], e1));
         }
-        __syncthreads();
-        C v[8];
+        const int at = cc * LS + pad8(r);
+        sm[at] = w0;
+        sm[fsm + at] = w1;
+        sm[2 * fsm + at] = w2;
+    }
+    __syncthreads();
+    C v[3][8];
+#pragma unroll
+    for (int f = 0; f < 3; ++f)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int r = t + T * q;
-            v[q] = r < n ? buf(r) : czero<C>();
-            v[q + 4] = czero<C>();
+            v[f][q] = r < n ? buf(f, r) : czero<C>();
+            v[f][q + 4] = czero<C>();
         }
-        __syncthreads();
-        fftr::fft_line<-1, L, true>(v, t, buf, sync, tw);
+    __syncthreads();
+    fftr::fft_lines<-1, L, true, 3>(v, t, buf, sync, tw);
 #pragma unroll
-        for (int q = 0; q < 8; ++q) buf(t + T * q) = v[q];
-        __syncthreads();
+    for (int f = 0; f < 3; ++f)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) buf(f, t + T * q) = v[f][q];
+    __syncthreads();
+    for (int f = 0; f < 3; ++f) {
         C *Wf = W + (b * 3 + f) * (long)L * n;
         for (int i = threadIdx.x; i < COLS * L; i += blockDim.x) {
             const int cc = i % COLS, r = i / COLS, i1 = col0 + cc;
-            if (i1 < n) Wf[(long)r * n + i1] = sm[cc * LS + pad8(r)];
+            if (i1 < n) Wf[(long)r * n + i1] = sm[f * fsm + cc * LS + pad8(r)];
         }
-        __syncthreads();
     }
 }
 
@@ -291,9 +299,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k2d_rowprod(typen
 
 // Pass 3, one column i1 < n per line, COLS adjacent columns per block: the
 // L rows of fields 0, 1 staged in shared memory (coalesced across columns),
-// inverse FFT along x2, rows i2 < n back through shared memory, y = x + result.
+// both inverse FFTs along x2 together, rows i2 < n back through shared memory,
+// y = x + result.
 template <typename R, int L>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256)
     k2d_colinv(const typename cplx_of<R>::type *__restrict__ W, const typename cplx_of<R>::type *__restrict__ x,
                typename cplx_of<R>::type *__restrict__ y, int n, const typename cplx_of<R>::type *__restrict__ tw,
                int COLS)
@@ -301,41 +310,44 @@ __global__ void __launch_bounds__(1024)
     using C = typename cplx_of<R>::type;
     constexpr int T = L / 8, LS = L + L / 8;
     extern __shared__ unsigned char smem_raw[];
-    C *sm = reinterpret_cast<C *>(smem_raw);
+    C *sm = reinterpret_cast<C *>(smem_raw); // [field][column][LS]
     const int c = threadIdx.x / T, t = threadIdx.x % T;
     const int col0 = blockIdx.x * COLS;
     const long b = blockIdx.y, N = (long)n * n;
-    C *lb = sm + c * LS;
-    auto buf = [&](int pos) -> C & { return lb[pad8(pos)]; };
+    const long fsm = (long)COLS * LS;
+    auto buf = [&](int k, int pos) -> C & { return sm[k * fsm + c * LS + pad8(pos)]; };
     auto sync = [&]() { __syncthreads(); };
-#pragma unroll 1
     for (int f = 0; f < 2; ++f) {
         const C *Wf = W + (b * 3 + f) * (long)L * n;
         for (int i = threadIdx.x; i < COLS * L; i += blockDim.x) {
             const int cc = i % COLS, r = i / COLS, i1 = col0 + cc;
-            sm[cc * LS + pad8(r)] = i1 < n ? Wf[(long)r * n + i1] : czero<C>();
+            sm[f * fsm + cc * LS + pad8(r)] = i1 < n ? Wf[(long)r * n + i1] : czero<C>();
         }
-        __syncthreads();
-        C v[8];
+    }
+    __syncthreads();
+    C v[2][8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) v[q] = buf(t + T * q);
-        __syncthreads();
-        fftr::fft_line<1, L, false>(v, t, buf, sync, tw);
+    for (int f = 0; f < 2; ++f)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[f][q] = buf(f, t + T * q);
+    __syncthreads();
+    fftr::fft_lines<1, L, false, 2>(v, t, buf, sync, tw);
+#pragma unroll
+    for (int f = 0; f < 2; ++f)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int r = t + T * q;
-            if (r < n) buf(r) = v[q];
+            if (r < n) buf(f, r) = v[f][q];
         }
-        __syncthreads();
+    __syncthreads();
+    for (int f = 0; f < 2; ++f)
         for (int i = threadIdx.x; i < COLS * n; i += blockDim.x) {
             const int cc = i % COLS, r = i / COLS, i1 = col0 + cc;
             if (i1 < n) {
                 const long o = (b * 2 + f) * N + (long)r * n + i1;
-                y[o] = x[o] + sm[cc * LS + pad8(r)];
+                y[o] = x[o] + sm[f * fsm + cc * LS + pad8(r)];
             }
         }
-        __syncthreads();
-    }
 }
 
 template <typename K> spm_status allow_smem(K kernel, size_t bytes)
@@ -361,12 +373,14 @@ spm_status apply_L(spm2_problem_s *P, const void *xv, void *yv, int nrhs, cudaSt
     C *W = P->work.as<C>();
     using G = Geo2<L>;
     // Columns per block of the column passes and rows per block of the row pass:
-    // as many as keep two blocks per SM busy (powers of two, at most 16
-    // columns and 1024 threads, at most 256 threads per row block).
+    // as many as keep two blocks per SM busy (powers of two, at most 16 columns
+    // and 512 (complex64) or 256 (complex128) threads, at most 256 threads per
+    // row block).
     auto pow2_floor = [](long v) { int r = 1; while ((long)r * 2 <= v) r *= 2; return r; };
-    const int cols = std::max(1, std::min({16, 1024 / G::T, pow2_floor(std::max(1L, (long)n / 304))}));
+    const int max_cols = std::max(1, (sizeof(R) == 4 ? 512 : 256) / G::T);
+    const int cols = std::max(1, std::min({16, max_cols, pow2_floor(std::max(1L, (long)n / 304))}));
     const int rb = std::max(1, std::min({L, std::max(1, 256 / G::T), pow2_floor(std::max(1L, (long)L / 304))}));
-    const size_t sm_rows = sizeof(C) * rb * 3 * G::LS, sm_cols = sizeof(C) * cols * G::LS;
+    const size_t sm_rows = sizeof(C) * rb * 3 * G::LS, sm_cols = sizeof(C) * 3 * cols * G::LS;
     SPM_TRY(allow_smem(k2d_colfwd<R, L>, sm_cols));
     SPM_TRY(allow_smem(k2d_rowprod<R, L>, sm_rows));
     SPM_TRY(allow_smem(k2d_colinv<R, L>, sm_cols));
