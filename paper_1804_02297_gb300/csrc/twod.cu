@@ -198,20 +198,35 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256)
     const long fsm = (long)COLS * LS;
     auto buf = [&](int k, int pos) -> C & { return sm[k * fsm + c * LS + pad8(pos)]; };
     auto sync = [&]() { __syncthreads(); };
-    for (int i = threadIdx.x; i < COLS * n; i += blockDim.x) {
-        const int cc = i % COLS, r = i / COLS, i1 = col0 + cc;
-        C w0 = czero<C>(), w1 = czero<C>(), w2 = czero<C>();
-        if (i1 < n) {
-            const long o = (long)r * n + i1;
-            const C mm = m[o], e0 = xb[o], e1 = xb[N + o];
-            w0 = cmul(mm, e0);
-            w1 = cmul(mm, e1);
-            w2 = cfma(p[o], e0, cmul(p[N + o], e1));
+    // every thread stages at most 4 points (COLS * n <= COLS * L / 2 = 4 blockDim.x):
+    // all loads first, then the shared-memory stores
+    {
+        C mm[4], e0[4], e1[4], p0[4], p1[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = q * blockDim.x + threadIdx.x;
+            const int cc = i & (COLS - 1), r = i / COLS, i1 = col0 + cc;
+            mm[q] = e0[q] = e1[q] = p0[q] = p1[q] = czero<C>();
+            if (r < n && i1 < n) {
+                const long o = (long)r * n + i1;
+                mm[q] = m[o];
+                e0[q] = xb[o];
+                e1[q] = xb[N + o];
+                p0[q] = p[o];
+                p1[q] = p[N + o];
+            }
         }
-        const int at = cc * LS + pad8(r);
-        sm[at] = w0;
-        sm[fsm + at] = w1;
-        sm[2 * fsm + at] = w2;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = q * blockDim.x + threadIdx.x;
+            const int cc = i & (COLS - 1), r = i / COLS;
+            if (r < n) {
+                const int at = cc * LS + pad8(r);
+                sm[at] = cmul(mm[q], e0[q]);
+                sm[fsm + at] = cmul(mm[q], e1[q]);
+                sm[2 * fsm + at] = cfma(p0[q], e0[q], cmul(p1[q], e1[q]));
+            }
+        }
     }
     __syncthreads();
     C v[3][8];
@@ -232,8 +247,10 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256)
     __syncthreads();
     for (int f = 0; f < 3; ++f) {
         C *Wf = W + (b * 3 + f) * (long)L * n;
-        for (int i = threadIdx.x; i < COLS * L; i += blockDim.x) {
-            const int cc = i % COLS, r = i / COLS, i1 = col0 + cc;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) { // COLS * L = 8 blockDim.x
+            const int i = q * blockDim.x + threadIdx.x;
+            const int cc = i & (COLS - 1), r = i / COLS, i1 = col0 + cc;
             if (i1 < n) Wf[(long)r * n + i1] = sm[f * fsm + cc * LS + pad8(r)];
         }
     }
@@ -317,12 +334,25 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256)
     const long fsm = (long)COLS * LS;
     auto buf = [&](int k, int pos) -> C & { return sm[k * fsm + c * LS + pad8(pos)]; };
     auto sync = [&]() { __syncthreads(); };
-    for (int f = 0; f < 2; ++f) {
-        const C *Wf = W + (b * 3 + f) * (long)L * n;
-        for (int i = threadIdx.x; i < COLS * L; i += blockDim.x) {
-            const int cc = i % COLS, r = i / COLS, i1 = col0 + cc;
-            sm[f * fsm + cc * LS + pad8(r)] = i1 < n ? Wf[(long)r * n + i1] : czero<C>();
+    {   // COLS * L = 8 blockDim.x elements per field: all 16 loads first
+        C t8[2][8];
+#pragma unroll
+        for (int f = 0; f < 2; ++f) {
+            const C *Wf = W + (b * 3 + f) * (long)L * n;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int i = q * blockDim.x + threadIdx.x;
+                const int cc = i & (COLS - 1), r = i / COLS, i1 = col0 + cc;
+                t8[f][q] = i1 < n ? Wf[(long)r * n + i1] : czero<C>();
+            }
         }
+#pragma unroll
+        for (int f = 0; f < 2; ++f)
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int i = q * blockDim.x + threadIdx.x;
+                sm[f * fsm + (i & (COLS - 1)) * LS + pad8(i / COLS)] = t8[f][q];
+            }
     }
     __syncthreads();
     C v[2][8];
@@ -340,14 +370,21 @@ __global__ void __launch_bounds__(sizeof(R) == 4 ? 512 : 256)
             if (r < n) buf(f, r) = v[f][q];
         }
     __syncthreads();
-    for (int f = 0; f < 2; ++f)
-        for (int i = threadIdx.x; i < COLS * n; i += blockDim.x) {
-            const int cc = i % COLS, r = i / COLS, i1 = col0 + cc;
-            if (i1 < n) {
-                const long o = (b * 2 + f) * N + (long)r * n + i1;
-                y[o] = x[o] + sm[f * fsm + cc * LS + pad8(r)];
-            }
+    for (int f = 0; f < 2; ++f) {
+        C xv[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) { // COLS * n <= 4 blockDim.x
+            const int i = q * blockDim.x + threadIdx.x;
+            const int cc = i & (COLS - 1), r = i / COLS, i1 = col0 + cc;
+            xv[q] = r < n && i1 < n ? x[(b * 2 + f) * N + (long)r * n + i1] : czero<C>();
         }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int i = q * blockDim.x + threadIdx.x;
+            const int cc = i & (COLS - 1), r = i / COLS, i1 = col0 + cc;
+            if (r < n && i1 < n) y[(b * 2 + f) * N + (long)r * n + i1] = xv[q] + sm[f * fsm + cc * LS + pad8(r)];
+        }
+    }
 }
 
 template <typename K> spm_status allow_smem(K kernel, size_t bytes)

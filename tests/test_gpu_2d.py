@@ -209,3 +209,59 @@ def test_preconditioned_solve(spm, n, medium, paper_iteration_counts_2d):
     assert rel(gh, ref_g) < 2e-11
     r = ref_g - op.apply(m, p, x.cpu().numpy()[0])
     assert np.linalg.norm(r) / np.linalg.norm(ref_g) < 2e-6
+
+
+def test_QA_composite_with_device_stencils(spm):
+    """Q A x with the stencils the device fitted, against the oracle's Q (with the same
+    tables) applied to the oracle's A x: complex128 to 2e-11, complex64 to 3e-5."""
+    n = 40
+    P, k, m, p = make(spm, n, "random")
+    P.build_stencils(spm.SPM_C128)
+    A, B, _ = P.get_stencils()
+    x = si.random_field_2d(n, 21)
+    ref = twod.apply_Q(n, A, twod.apply_fft(n, k, m, p, x))
+    for dt, tol in ((torch.complex128, 2e-11), (torch.complex64, 3e-5)):
+        y = torch.zeros(x.shape, dtype=dt, device="cuda")
+        P.apply_QA(to_dev(x, dt), y)
+        torch.cuda.synchronize()
+        err = rel(y.cpu().numpy().astype(np.complex128), ref)
+        assert err < tol, (dt, err)
+
+
+def test_stencils_at_paper_size(spm):
+    """n = 119 (k/2pi = 20, the first row of Tables 1-3): interior, edge and corner
+    classes against the oracle (singular values and the basis-free projector)."""
+    n = 119
+    P, k, m, p = make(spm, n, "lens")
+    P.build_stencils(spm.SPM_C128)
+    A, B, SV = P.get_stencils()
+    for cls in (4, 1, 0, 8):
+        a, b, sv = twod.class_stencil(n, k, cls)
+        T = a.shape[0] // 2
+        assert np.allclose(SV[cls, :2 * T], sv, rtol=1e-6, atol=1e-9 * sv[-1]), cls
+        P1 = A[cls, :2 * T].conj() @ A[cls, :2 * T].T
+        P2 = a.conj() @ a.T
+        assert np.linalg.norm(P1 - P2) < 1e-7 / min(sv[2] / sv[1] - 1, 1.0), cls
+
+
+def test_mixed_solve_and_several_rhs(spm):
+    """Mixed precision (complex64 operator and factor inside the FP64 outer loop) at
+    n = 59 on two right-hand sides at once (the plane wave and its mirror image), each
+    reaching 1e-6 and agreeing with the FP64 solve."""
+    n = 59
+    wl = si.workload_2d(f"lens2d_n{n}")
+    k = wl["omega"]
+    P = spm.Problem2D(n, k, wl["eps"], wl["grad"])
+    P.build_stencils(spm.SPM_C64)
+    P.factor_S(spm.SPM_C128)
+    e = np.concatenate([wl["einc"], wl["einc"][:, :, :, ::-1].copy()])
+    einc = to_dev(e)
+    g = torch.zeros_like(einc)
+    P.rhs_from_incident(einc, g)
+    x = torch.zeros_like(g)
+    info, st = P.solve(g, x, prec=spm.SPM_MIXED, tol=1e-6)
+    assert st == 0 and info.true_relres <= 1e-6
+    x2 = torch.zeros_like(g)
+    info2, st2 = P.solve(g, x2, prec=spm.SPM_C128, tol=1e-9)
+    assert st2 == 0 and info2.true_relres <= 1e-9
+    assert rel(x.cpu().numpy(), x2.cpu().numpy()) < 1e-5
