@@ -812,30 +812,36 @@ def run_ours(args):
     dist = torch.distributed if world > 1 else None
     ms_per_step, value = aggregate_timing(total_ms, args.steps, nrhs, world, dist, "cuda")
 
-    # e2e: pinned host input -> device -> apply -> host, every step
-    xh = torch.from_numpy(wl["einc"]).to(dtype).pin_memory()
+    # e2e: the host-buffer C-ABI call (spm_apply_QA_host / spm_apply_A_host): every
+    # step's fields start in page-locked host memory and its results end there;
+    # the library overlaps the copies of one field with the apply of the previous
+    # one.  Calls of up to 32 steps each, the K steps timed as a whole.
+    per_call = max(1, 32 // nrhs)
+    x0 = torch.from_numpy(wl["einc"]).to(dtype)
+    xh = x0.repeat(per_call, 1, 1, 1, 1).contiguous().pin_memory()
     yh = torch.empty_like(xh).pin_memory()
-    xd = torch.empty_like(x)
-    for _ in range(2):
-        xd.copy_(xh, non_blocking=True)
-        fn(xd, y)
-        yh.copy_(y, non_blocking=True)
+    host_fn = P.apply_QA_host if args.op == "QA" else P.apply_A_host
+    host_fn(xh[:nrhs], yh[:nrhs])
+    host_fn(xh, yh)
     torch.cuda.synchronize()
-    ev = []
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        xd.copy_(xh, non_blocking=True)
-        fn(xd, y)
-        yh.copy_(y, non_blocking=True)
-        e1.record(stream)
-        ev.append((e0, e1))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    done = 0
+    while done < args.steps:
+        cnt = min(per_call, args.steps - done)
+        host_fn(xh[: cnt * nrhs], yh[: cnt * nrhs])
+        done += cnt
+    e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = float(np.sum([a.elapsed_time(b) for a, b in ev]))
+    e2e_ms = e0.elapsed_time(e1)
     _, e2e_value = aggregate_timing(e2e_ms, args.steps, nrhs, world, dist, "cuda")
-    nbytes = xh.numel() * xh.element_size()
+    # the host result equals the device result of the same input
+    ref = torch.empty_like(x)
+    fn(x, ref)
+    torch.cuda.synchronize()
+    e2e_check = float((yh[:nrhs].to("cuda") - ref).abs().max() / ref.abs().max())
+    nbytes = x0.numel() * x0.element_size()  # one step's fields (copied in, and the results out)
 
     peak, peak_kind = peaks()
     alg = compulsory_bytes(n, args.prec, nrhs)
@@ -873,7 +879,9 @@ def run_ours(args):
                        "parallelism": f"replicas{world}"},
             "roofline": roof,
             "e2e": {"value": e2e_value, "unit": "field applies/s" if nrhs > 1 else "applies/s",
-                    "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+                    "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+                    "api": "spm_apply_QA_host" if args.op == "QA" else "spm_apply_A_host",
+                    "steps_per_call": per_call, "max_rel_diff_vs_device_call": e2e_check},
             "gpu_launches": launches_per_step * args.steps * max(1, -(-nrhs // chunk_of(P, n, args.prec))),
             "clocks": clocks,
             "step_ms_min": float(np.min(step_ms)), "step_ms_median": float(np.median(step_ms))}

@@ -134,6 +134,20 @@ spm_status spm_apply_A_cufft(spm_problem prob, spm_prec prec, const void *x_dev,
 spm_status spm_apply_QA(spm_problem prob, spm_prec prec, const void *x_dev, void *y_dev,
                         int nrhs, void *stream);
 
+/* y = A x (spm_apply_A_host) or y = Q A x (spm_apply_QA_host) for nrhs fields
+ * held in HOST memory (x_host, y_host: nrhs x 3 x n^3 complex in `prec`, the
+ * layout of the device calls).  Each field is copied to the device, applied on
+ * `stream`, and copied back; the copies of one field overlap the apply of the
+ * previous one (two device slots, host-to-device and device-to-host copies on two
+ * library streams), so page-locked host memory lets the transfers hide behind the
+ * applies (pageable memory works but serialises the copies).  Same arithmetic as
+ * the device calls.  Synchronises `stream`: y_host is complete on return.
+ * Device scratch of four fields is allocated for the call and freed on return. */
+spm_status spm_apply_A_host(spm_problem prob, spm_prec prec, const void *x_host, void *y_host, int nrhs,
+                            void *stream);
+spm_status spm_apply_QA_host(spm_problem prob, spm_prec prec, const void *x_host, void *y_host, int nrhs,
+                             void *stream);
+
 /* y = Q v (the row combination alone), same layout and requirements. */
 spm_status spm_apply_Q(spm_problem prob, spm_prec prec, const void *v_dev, void *y_dev,
                        int nrhs, void *stream);

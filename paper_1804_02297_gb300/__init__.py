@@ -28,7 +28,7 @@ EXPORTS = [
     "spm_lattice_constant", "spm_last_error", "spm_apply_A_noalloc",
     "spm_create_batch", "spm_destroy_batch", "spm_batch_size", "spm_batch_problem", "spm_batch_build_stencils",
     "spm_batch_apply_A", "spm_batch_solve", "spm_measure_peak", "spm_apply_A_cufft",
-    "spm_save_apply_plans", "spm_load_apply_plans", "spm_profile_apply",
+    "spm_save_apply_plans", "spm_load_apply_plans", "spm_profile_apply", "spm_apply_A_host", "spm_apply_QA_host",
     "spm2_create_problem", "spm2_destroy", "spm2_problem_info", "spm2_lattice_zeta_prime", "spm2_kernel_entries",
     "spm2_apply_A", "spm2_apply_Q", "spm2_apply_QA", "spm2_build_stencils", "spm2_set_stencils",
     "spm2_get_stencils", "spm2_apply_S", "spm2_factor_S", "spm2_factor_info", "spm2_solve_S",
@@ -107,6 +107,8 @@ def _load():
         "spm_profile_apply": [P, I, P, P, I, I, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(I), P],
         "spm_load_apply_plans": [ctypes.c_char_p, ctypes.POINTER(I)],
         "spm_apply_QA": [P, I, P, P, I, P],
+        "spm_apply_A_host": [P, I, P, P, I, P],
+        "spm_apply_QA_host": [P, I, P, P, I, P],
         "spm_apply_Q": [P, I, P, P, I, P],
         "spm_build_stencils": [P, I],
         "spm_set_stencils": [P, P, P],
@@ -205,8 +207,12 @@ def _stream(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
+def _numel(x):
+    return x.numel() if hasattr(x, "numel") else x.size
+
+
 def _nrhs(x, n):
-    return x.numel() // (3 * n ** 3)
+    return _numel(x) // (3 * n ** 3)
 
 
 def spm_lattice_constant() -> float:
@@ -281,6 +287,17 @@ class Problem:
 
     def apply_Q(self, v, y, stream=None):
         _check(lib.spm_apply_Q(self.h, _prec_of(v), _ptr(v), _ptr(y), _nrhs(v, self.n), _stream(stream)))
+        return y
+
+    def apply_A_host(self, x, y, stream=None):
+        """y = A x with x, y in host memory (numpy arrays or pinned CPU tensors); the
+        transfers of one field overlap the apply of the previous one."""
+        _check(lib.spm_apply_A_host(self.h, _prec_of(x), _ptr(x), _ptr(y), _nrhs(x, self.n), _stream(stream)))
+        return y
+
+    def apply_QA_host(self, x, y, stream=None):
+        """y = Q A x with x, y in host memory (as apply_A_host)."""
+        _check(lib.spm_apply_QA_host(self.h, _prec_of(x), _ptr(x), _ptr(y), _nrhs(x, self.n), _stream(stream)))
         return y
 
     # ---- stencils and S
@@ -424,7 +441,7 @@ class Batch:
 # ------------------------------------------------------------------ 2-D variant
 
 def _nrhs2(x, n):
-    return x.numel() // (2 * n * n)
+    return _numel(x) // (2 * n * n)
 
 
 def spm2_lattice_zeta_prime() -> float:

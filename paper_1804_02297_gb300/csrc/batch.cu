@@ -126,7 +126,32 @@ extern "C" spm_status spm_batch_problem(spm_batch B, int index, spm_problem *out
 extern "C" spm_status spm_batch_build_stencils(spm_batch B, spm_prec factor_prec)
 {
     if (!B) { spm_set_error("NULL batch"); return SPM_ERR_INVALID_ARG; }
-    return parallel_for((int)B->probs.size(), [&](int i) { return spm_build_stencils(B->probs[i], factor_prec); });
+    // Up to 8 problems are factored at once, each with its own front and update
+    // workspaces; a problem whose workspace did not fit beside the others is
+    // factored again afterwards, alone.
+    const int count = (int)B->probs.size();
+    std::vector<int> status(count, SPM_OK);
+    parallel_for(count, [&](int i) -> spm_status {
+        status[i] = spm_build_stencils(B->probs[i], factor_prec);
+        return status[i] == SPM_ERR_OOM ? SPM_OK : (spm_status)status[i];
+    });
+    for (int i = 0; i < count; ++i)
+        if (status[i] != SPM_OK && status[i] != SPM_ERR_OOM) {
+            spm_set_error("problem %d: build failed (status %d)", i, status[i]);
+            return (spm_status)status[i];
+        }
+    for (int i = 0; i < count; ++i)
+        if (status[i] == SPM_ERR_OOM) {
+            cudaDeviceSynchronize();
+            spm_status st = spm_build_stencils(B->probs[i], factor_prec);
+            if (st != SPM_OK) {
+                char msg[1024];
+                snprintf(msg, sizeof(msg), "problem %d: %s", i, spm_last_error());
+                spm_set_error("%s", msg);
+                return st;
+            }
+        }
+    return SPM_OK;
 }
 
 extern "C" spm_status spm_batch_apply_A(spm_batch B, spm_prec prec, const void *const *x_dev, void *const *y_dev,

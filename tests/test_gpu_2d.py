@@ -265,3 +265,18 @@ def test_mixed_solve_and_several_rhs(spm):
     info2, st2 = P.solve(g, x2, prec=spm.SPM_C128, tol=1e-9)
     assert st2 == 0 and info2.true_relres <= 1e-9
     assert rel(x.cpu().numpy(), x2.cpu().numpy()) < 1e-5
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_apply_order2_quadrature(spm, prec):
+    """The punctured-trapezoid entries (SPM_QUAD_ORDER2) through the whole apply."""
+    n = 30
+    P, k, m, p = make(spm, n, "random", quad=spm.SPM_QUAD_ORDER2)
+    x = si.random_field_2d(n, 23, 2)
+    ref = twod.apply_fft(n, k, m, p, x, quad=twod.QUAD_ORDER2)
+    dt = torch.complex128 if prec == "c128" else torch.complex64
+    y = torch.zeros(x.shape, dtype=dt, device="cuda")
+    P.apply_A(to_dev(x, dt), y)
+    torch.cuda.synchronize()
+    err = rel(y.cpu().numpy().astype(np.complex128), ref)
+    assert err < (2e-11 if prec == "c128" else 2e-5), err

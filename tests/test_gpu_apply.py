@@ -350,3 +350,28 @@ def test_profile_apply_times_every_pass(spm):
     torch.cuda.synchronize()
     assert torch.equal(y, ref)
     assert len(P.profile_apply(x, y, with_q=False, reps=2)) == (3 if zv & 8 else 5)
+
+
+@pytest.mark.parametrize("dtype", [torch.complex128, torch.complex64])
+def test_host_buffer_applies_match_device_calls(spm, dtype):
+    """spm_apply_A_host / spm_apply_QA_host (fields in page-locked host memory, copies
+    overlapped with the applies) give the device calls' results, bit for bit, on
+    several right-hand sides; pageable (numpy) buffers too."""
+    n = 16
+    P, k, m, p = make(spm, n, "bumps")
+    al, be, _ = oracle.all_stencils(n, k)
+    P.set_stencils(al, be)
+    x = si.random_field(n, 31, 5)
+    xd = to_dev(x, dtype)
+    for dev_fn, host_fn in ((P.apply_A, P.apply_A_host), (P.apply_QA, P.apply_QA_host)):
+        yd = torch.zeros_like(xd)
+        dev_fn(xd, yd)
+        torch.cuda.synchronize()
+        xh = xd.cpu().pin_memory()
+        yh = torch.zeros_like(xh).pin_memory()
+        host_fn(xh, yh)
+        assert torch.equal(yh, yd.cpu())
+        xn = xd.cpu().numpy()
+        yn = np.zeros_like(xn)
+        host_fn(xn, yn)
+        assert np.array_equal(yn, yd.cpu().numpy())
