@@ -192,11 +192,14 @@ extern "C" spm_status spm_create_problem(int n, double omega, const double *eps_
             return fail(SPM_ERR_CUDA);
         }
     }
-    // right-hand sides per pass chunk: keep one chunk's intermediates (24 n^3
-    // complex per RHS) within about half of the 129 MB L2
+    // right-hand sides per pass chunk: the passes are latency-bound at these
+    // sizes, so more right-hand sides per launch (larger grids) pay even when a
+    // chunk's intermediates (24 n^3 complex per RHS) leave the L2; up to 4 GB of
+    // intermediates per chunk (64 RHS at n = 64: 17.9k field applies/s against
+    // 14.9k with the chunk kept within half of the L2; 8 RHS at n = 128: +5 %)
     {
         const double per64 = 24.0 * n3 * 8, per128 = 24.0 * n3 * 16;
-        const double budget = 64.0 * 1024 * 1024;
+        const double budget = 4096.0 * 1024 * 1024;
         P->chunk64 = per64 >= budget ? 1 : (int)(budget / per64);
         P->chunk128 = per128 >= budget ? 1 : (int)(budget / per128);
         if (P->chunk64 > 64) P->chunk64 = 64;
