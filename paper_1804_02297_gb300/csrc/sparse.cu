@@ -119,14 +119,17 @@ template <typename C>
 __global__ void __launch_bounds__(256) k_front_batch(const BatchFront *__restrict__ fronts, const C *__restrict__ S,
                                                      const int *__restrict__ pts, const int *__restrict__ maps,
                                                      const int *__restrict__ rels, GridDesc g, C *fac, double tau,
-                                                     int *raised)
+                                                     int *raised, C *gscratch, long gstride)
 {
     using R = decltype(C{}.x);
     extern __shared__ unsigned char smem_raw[];
     const BatchFront fr = fronts[blockIdx.x];
     const int f = fr.f, o3 = fr.o3, b3 = f - o3;
-    C *F = reinterpret_cast<C *>(smem_raw); // f x f, column-major: row r, column c at c * f + r
-    C *prow = F + (long)f * f;              // the scaled pivot row
+    // the front, f x f column-major (row r, column c at c * f + r): in shared memory,
+    // or for larger fronts in this block's slice of a global scratch (then only the
+    // pivot row, pivot column and permutation sit in shared memory)
+    C *F = gscratch ? gscratch + (long)blockIdx.x * gstride : reinterpret_cast<C *>(smem_raw);
+    C *prow = gscratch ? reinterpret_cast<C *>(smem_raw) : F + (long)f * f; // the scaled pivot row
     C *pcol = prow + f;                     // the pivot column before the step
     int *perm = reinterpret_cast<int *>(pcol + f);
     __shared__ R red_v[8];
@@ -670,7 +673,8 @@ static spm_status factor_typed(const SparseSys &SY, NDFactor *F, bool half_store
     // Small fronts (f <= BATCH_FMAX, whose whole subtree is small) are factored
     // first, level by level, each level in one launch of k_front_batch; their
     // updates go to buffers of their own.  The stream pool below handles the rest.
-    const int BATCH_FMAX = sizeof(R) == 8 ? 112 : 160;
+    const int BATCH_FMAX_SMEM = sizeof(R) == 8 ? 112 : 160; // whole front in shared memory
+    const int BATCH_FMAX = 512;                               // larger fronts: global scratch
     std::vector<char> batched(NN, 0);
     for (int id = 0; id < NN; ++id) { // postorder: children before parents
         const Node &nd = nodes[id];
@@ -799,27 +803,54 @@ static spm_status factor_typed(const SparseSys &SY, NDFactor *F, bool half_store
             ++nbf;
         }
         if (nbf > 0) {
+            // per level: the fronts that fit shared memory, then the larger ones
             SPM_TRY(batch_desc.ensure(sizeof(BatchFront) * nbf));
             std::vector<BatchFront> all;
-            std::vector<std::pair<size_t, size_t>> range(maxd + 1);
+            struct Launch { size_t first, count; int fm; bool global; };
+            std::vector<Launch> launches;
+            size_t scratch_max = 0;
             for (int d = maxd; d >= 0; --d) {
-                range[d] = {all.size(), lv[d].size()};
-                all.insert(all.end(), lv[d].begin(), lv[d].end());
+                for (int pass = 0; pass < 2; ++pass) {
+                    Launch ln{all.size(), 0, 1, pass == 1};
+                    for (const BatchFront &b : lv[d])
+                        if ((b.f > BATCH_FMAX_SMEM) == (pass == 1)) {
+                            all.push_back(b);
+                            ++ln.count;
+                            ln.fm = std::max(ln.fm, b.f);
+                        }
+                    if (ln.count == 0) continue;
+                    if (ln.global) { // chunks of at most 2 GB of scratch
+                        const size_t per = (size_t)ln.fm * ln.fm;
+                        const size_t chunk = std::max<size_t>(1, ((size_t)2 << 30) / (sizeof(C) * per));
+                        for (size_t c0 = 0; c0 < ln.count; c0 += chunk) {
+                            Launch part = ln;
+                            part.first = ln.first + c0;
+                            part.count = std::min(chunk, ln.count - c0);
+                            scratch_max = std::max(scratch_max, part.count * per);
+                            launches.push_back(part);
+                        }
+                    } else {
+                        launches.push_back(ln);
+                    }
+                }
             }
             SPM_CUDA_TRY(cudaMemcpy(batch_desc.ptr, all.data(), sizeof(BatchFront) * nbf, cudaMemcpyHostToDevice));
-            const size_t smem_max = sizeof(C) * ((size_t)BATCH_FMAX * BATCH_FMAX + 2 * BATCH_FMAX) + sizeof(int) * BATCH_FMAX;
+            DevBuf gscratch;
+            if (scratch_max > 0) SPM_TRY(gscratch.ensure(sizeof(C) * scratch_max));
+            const size_t smem_max = sizeof(C) * ((size_t)BATCH_FMAX_SMEM * BATCH_FMAX_SMEM + 2 * BATCH_FMAX_SMEM) +
+                                    sizeof(int) * BATCH_FMAX_SMEM;
             SPM_CUDA_TRY(cudaFuncSetAttribute(k_front_batch<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
             const GridDesc gd2{n1, n2, n3d, D, SY.nsten};
-            for (int d = maxd; d >= 0; --d) {
-                if (range[d].second == 0) continue;
-                int fm = 1;
-                for (const BatchFront &b : lv[d]) fm = std::max(fm, b.f);
-                const size_t smem = sizeof(C) * ((size_t)fm * fm + 2 * fm) + sizeof(int) * fm;
-                k_front_batch<C><<<(unsigned)range[d].second, 256, smem, s>>>(
-                    batch_desc.as<BatchFront>() + range[d].first, Sdev, dpts, dmaps, drels, gd2, fac, pivot_floor<R>(),
-                    dinfo + 2);
+            for (const Launch &ln : launches) {
+                const size_t fm = (size_t)ln.fm;
+                const size_t smem = ln.global ? sizeof(C) * 2 * fm + sizeof(int) * fm
+                                              : sizeof(C) * (fm * fm + 2 * fm) + sizeof(int) * fm;
+                k_front_batch<C><<<(unsigned)ln.count, 256, smem, s>>>(
+                    batch_desc.as<BatchFront>() + ln.first, Sdev, dpts, dmaps, drels, gd2, fac, pivot_floor<R>(),
+                    dinfo + 2, ln.global ? gscratch.as<C>() : nullptr, (long)(fm * fm));
             }
             SPM_CUDA_TRY(cudaGetLastError());
+            if (scratch_max > 0) SPM_CUDA_TRY(cudaStreamSynchronize(s)); // before the scratch is freed
         }
     }
     // per-slot buffers and streams (slot ngroups - 1 is the problem's stream)
