@@ -1132,7 +1132,6 @@ extern "C" spm_status spm2_solve(spm2_problem P, spm_prec prec, const void *g, v
     ops.apply_A = ops2_A;
     ops.apply_Q = ops2_Q;
     ops.solve_S = ops2_S;
-    SPM_TRY(P->kry.ensure(0));
     spm_solve_info local{};
     spm_solve_info *inf = info ? info : &local;
     cudaEvent_t e0, e1;
