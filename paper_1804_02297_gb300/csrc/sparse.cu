@@ -133,7 +133,6 @@ __global__ void __launch_bounds__(256) k_front_batch(const BatchFront *__restric
     C *pcol = prow + f;                     // the pivot column before the step
     int *perm = reinterpret_cast<int *>(pcol + f);
     __shared__ R red_v[8];
-    __shared__ int red_i[8];
     __shared__ R s_floor;
     __shared__ int s_p;
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
