@@ -368,7 +368,7 @@ def test_born_limit():
 
 
 def test_preconditioner_cuts_iterations(paper_iteration_counts):
-    """Behaviour (parity unpinned): S^{-1}Q-preconditioned GMRES needs few iterations.
+    """Behaviour, not a parity pin: S^{-1}Q-preconditioned GMRES needs few iterations.
     The paper's 3-D tables (tests/golden/paper_iteration_counts.txt, Tables 4-6)
     print 6 or 7 iterations for every medium and size, and the paper states that
     every case needs fewer than ten; the oracle's count on a Gaussian lens must

@@ -184,6 +184,39 @@ def test_direct_sum_equals_fft_apply(n, L):
     assert np.linalg.norm(yd - yf) / np.linalg.norm(yd) < 1e-13
 
 
+def test_toeplitz_reciprocity():
+    """The weights G_t are even in t and G^d_t odd in t_d (Section 2: G depends on |x|,
+    G^d = d_d G), so u^T (G * v) = v^T (G * u) and u^T (G^d * v) = -v^T (G^d * u).
+    An embedding index off by one, or a kernel that lost its parity, breaks one identity."""
+    n, k = 9, 4.0
+    u = si.random_field_2d(n, 5)[0]
+    v = si.random_field_2d(n, 6)[0]
+    a = np.sum(u * twod.convolve(n, k, 0, v))
+    b = np.sum(v * twod.convolve(n, k, 0, u))
+    assert abs(a - b) < 1e-13 * abs(a)
+    for d in (1, 2):
+        a = np.sum(u * twod.convolve(n, k, d, v))
+        b = np.sum(v * twod.convolve(n, k, d, u))
+        assert abs(a + b) < 1e-12 * abs(a)
+
+
+def test_born_limit():
+    """A contrast scaled by s gives A = I + O(s), hence E^s = g + O(s^2) for g = E^i - A E^i
+    = O(s): ||E^s - g|| / ||g|| falls linearly with s (the first Born approximation)."""
+    n = 8
+    k = si.wavenumber_for_grid_2d(n)
+    eps, grad = si.random_medium_2d(n, 7)
+    einc = si.plane_wave_2d(n, k)
+    op = twod.FFTOperator(n, k)
+    ratios = []
+    for s in (1e-2, 5e-3):
+        m, p = twod.medium(1 + s * (eps - 1), s * grad)
+        g = einc - op.apply(m, p, einc)
+        x, _, _ = twod.gmres(lambda v: op.apply(m, p, v), g, tol=1e-13, restart=40, maxit=400)
+        ratios.append(np.linalg.norm(x - g) / np.linalg.norm(g))
+    assert 1.7 < ratios[0] / ratios[1] < 2.3
+
+
 def test_dense_matches_direct_apply():
     n, k = 6, 4.0
     m, p = _medium(n, 5)
@@ -304,7 +337,7 @@ def test_gmres_matches_dense_solve():
 
 @pytest.mark.slow
 def test_preconditioner_iterations_2d(paper_iteration_counts_2d):
-    """Behaviour (parity unpinned): Section 4's 2-D Tables 1-3 print 6-9 iterations
+    """Behaviour, not a parity pin: Section 4's 2-D Tables 1-3 print 6-9 iterations
     of S^{-1}Q-preconditioned GMRES(20) to 1e-6 at six points per wavelength.  The
     oracle's counts on the three synthetic stand-ins at n = 59 (k/2pi = 10) must stay
     under the tables' maximum and well under the unpreconditioned counts."""
