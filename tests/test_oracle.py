@@ -304,6 +304,26 @@ def test_sparse_rows_equal_QA_on_pattern():
     assert np.linalg.norm(QA[~pattern]) < 0.5 * np.linalg.norm(QA[pattern])
 
 
+def test_preconditioner_is_basis_free():
+    """Reading C3: any alpha' = alpha R (R invertible, one per class) with beta' = beta R
+    gives Q' = R^T Q and S' = R^T S point by point, so S'^{-1} Q' v = S^{-1} Q v.  Q and the
+    assembly of S must index alpha's columns alike for this to hold; a transposed,
+    conjugated or mis-indexed alpha in either one breaks it."""
+    n, k = 4, 3.0
+    m, p = _medium(n, seed=13)
+    al, be, _ = oracle.all_stencils(n, k)
+    rng = np.random.default_rng(21)
+    R = rng.standard_normal((27, 3, 3)) + 1j * rng.standard_normal((27, 3, 3)) + 2 * np.eye(3)
+    al2 = np.einsum("cti,cij->ctj", al, R)
+    be2 = np.einsum("cti,cij->ctj", be, R)
+    v = si.random_field(n, 14)
+    y1 = oracle.dense_solve(oracle.dense_S(n, m, p, al, be), oracle.apply_Q(n, al, v).ravel())
+    y2 = oracle.dense_solve(oracle.dense_S(n, m, p, al2, be2), oracle.apply_Q(n, al2, v).ravel())
+    assert np.linalg.norm(y1 - y2) < 1e-10 * np.linalg.norm(y1)
+    # the tables really changed
+    assert np.linalg.norm(oracle.apply_Q(n, al2, v) - oracle.apply_Q(n, al, v)) > 0.1 * np.linalg.norm(v)
+
+
 def test_apply_Q_matches_brute_force():
     n = 4
     al = si.random_field(1, 9, 27 * 81 * 3 // 3).reshape(-1)[: 27 * 81 * 3].reshape(27, 81, 3)

@@ -318,6 +318,25 @@ def test_sparse_rows_equal_QA_on_pattern():
     assert nnz_rows.min() == 2 * 4 and nnz_rows.max() == 2 * 9
 
 
+def test_preconditioner_is_basis_free():
+    """Reading C3 in 2-D: alpha' = alpha R, beta' = beta R (R invertible, one per class)
+    give S'^{-1} Q' v = S^{-1} Q v, since Q' = R^T Q and S' = R^T S point by point; it
+    holds only if Q and the assembly of S index alpha's columns alike."""
+    from scipy.sparse.linalg import spsolve
+    n, k = 6, 2 * np.pi
+    m, p = _medium(n, 13)
+    al, be, _ = twod.all_stencils(n, k)
+    rng = np.random.default_rng(21)
+    R = rng.standard_normal((9, 2, 2)) + 1j * rng.standard_normal((9, 2, 2)) + 2 * np.eye(2)
+    al2 = np.einsum("cti,cij->ctj", al, R)
+    be2 = np.einsum("cti,cij->ctj", be, R)
+    v = si.random_field_2d(n, 14)
+    y1 = spsolve(twod.sparse_S(n, m, p, al, be).tocsc(), twod.apply_Q(n, al, v).ravel())
+    y2 = spsolve(twod.sparse_S(n, m, p, al2, be2).tocsc(), twod.apply_Q(n, al2, v).ravel())
+    assert np.linalg.norm(y1 - y2) < 1e-10 * np.linalg.norm(y1)
+    assert np.linalg.norm(twod.apply_Q(n, al2, v) - twod.apply_Q(n, al, v)) > 0.1 * np.linalg.norm(v)
+
+
 def test_gmres_matches_dense_solve():
     """Restarted GMRES (with and without S^{-1}Q) reaches the dense solution of Eq. discrete."""
     n, k = 8, 2 * np.pi
